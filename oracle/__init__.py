@@ -1,0 +1,203 @@
+"""FP64 CPU oracle for the implicit FLD radiation step (Guangqi, Sec. 3.2).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import this package.  It is a plain, slow C
+implementation (``gq_oracle.c``) that shares no code with the CUDA library; this
+module only marshals numpy arrays into it.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("coord", ctypes.c_int),
+        ("xf", _dp), ("yf", _dp), ("V_in", _dp), ("Ax_in", _dp), ("Ay_in", _dp),
+        ("rho", _dp), ("eg", _dp), ("E", _dp),
+        ("kR", ctypes.c_double * 4), ("kP", ctypes.c_double * 4),
+        ("gamma", ctypes.c_double), ("mu", ctypes.c_double), ("dt", ctypes.c_double),
+        ("bc", ctypes.c_int * 4), ("limiter", ctypes.c_int),
+    ]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            P = ctypes.POINTER(_Problem)
+            L.orc_limiter.restype = ctypes.c_double
+            L.orc_limiter.argtypes = [ctypes.c_int, ctypes.c_double]
+            for name in ("orc_const_c", "orc_const_aR", "orc_const_kB", "orc_const_mH"):
+                getattr(L, name).restype = ctypes.c_double
+                getattr(L, name).argtypes = []
+            L.orc_geometry.argtypes = [P, _dp, _dp, _dp, _dp, _dp]
+            L.orc_faces.argtypes = [P, _dp, _dp, _dp, _dp, _dp, _dp]
+            L.orc_assemble_coupled.argtypes = [P, _ip, _ip, _dp, _dp]
+            L.orc_assemble_reduced.argtypes = [P, _ip, _ip, _dp, _dp]
+            L.orc_band_solve.argtypes = [ctypes.c_int, _ip, _ip, _dp, _dp, _dp]
+            L.orc_pcg.argtypes = [ctypes.c_int, _ip, _ip, _dp, _dp, _dp, ctypes.c_double, ctypes.c_int,
+                                  _ip, _dp]
+            L.orc_step.argtypes = [P, ctypes.c_int, ctypes.c_double, _dp, _dp, _dp, _dp, _dp, _dp]
+            _lib = L
+    return _lib
+
+
+def _d(a: Optional[np.ndarray]):
+    if a is None:
+        return ctypes.cast(None, _dp)
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_dp)
+
+
+def _i(a: np.ndarray):
+    assert a.dtype == np.int32 and a.flags.c_contiguous
+    return a.ctypes.data_as(_ip)
+
+
+class _Bound:
+    """Keeps the numpy arrays referenced by a _Problem alive."""
+
+    def __init__(self, prob, V=None, Ax=None, Ay=None):
+        self.arrs = [np.ascontiguousarray(prob.x_faces, dtype=np.float64),
+                     np.ascontiguousarray(prob.y_faces, dtype=np.float64),
+                     None if V is None else np.ascontiguousarray(V, dtype=np.float64),
+                     None if Ax is None else np.ascontiguousarray(Ax, dtype=np.float64),
+                     None if Ay is None else np.ascontiguousarray(Ay, dtype=np.float64),
+                     np.ascontiguousarray(prob.rho, dtype=np.float64),
+                     np.ascontiguousarray(prob.e_g, dtype=np.float64),
+                     np.ascontiguousarray(prob.E_r, dtype=np.float64)]
+        xf, yf, V_, Ax_, Ay_, rho, eg, E = self.arrs
+        s = _Problem()
+        s.nx, s.ny, s.coord = prob.nx, prob.ny, int(prob.coord)
+        s.xf, s.yf, s.V_in, s.Ax_in, s.Ay_in = _d(xf), _d(yf), _d(V_), _d(Ax_), _d(Ay_)
+        s.rho, s.eg, s.E = _d(rho.ravel()), _d(eg.ravel()), _d(E.ravel())
+        for t in range(4):
+            s.kR[t] = float(prob.opacity_R[t])
+            s.kP[t] = float(prob.opacity_P[t])
+            s.bc[t] = int(prob.bc[t])
+        s.gamma, s.mu, s.dt = float(prob.gamma), float(prob.mu), float(prob.dt)
+        s.limiter = int(prob.limiter)
+        self.s = s
+
+    def ref(self):
+        return ctypes.byref(self.s)
+
+
+def constants() -> dict:
+    L = lib()
+    return {"c": L.orc_const_c(), "aR": L.orc_const_aR(), "kB": L.orc_const_kB(), "mH": L.orc_const_mH()}
+
+
+def limiter(kind: int, R) -> np.ndarray:
+    L = lib()
+    R = np.atleast_1d(np.asarray(R, dtype=np.float64))
+    return np.array([L.orc_limiter(int(kind), float(r)) for r in R.ravel()]).reshape(R.shape)
+
+
+def geometry(prob, V=None, Ax=None, Ay=None) -> dict:
+    nx, ny = prob.nx, prob.ny
+    out = {"V": np.zeros((ny, nx)), "Ax": np.zeros((ny, nx + 1)), "Ay": np.zeros((ny + 1, nx)),
+           "xc": np.zeros(nx), "yc": np.zeros(ny)}
+    b = _Bound(prob, V, Ax, Ay)
+    rc = lib().orc_geometry(b.ref(), _d(out["V"]), _d(out["Ax"]), _d(out["Ay"]), _d(out["xc"]), _d(out["yc"]))
+    if rc:
+        raise RuntimeError(f"orc_geometry failed ({rc})")
+    return out
+
+
+def faces(prob, V=None, Ax=None, Ay=None) -> dict:
+    nx, ny = prob.nx, prob.ny
+    out = {k: np.zeros((ny, nx + 1)) for k in ("Rx", "Dx", "wx")}
+    out.update({k: np.zeros((ny + 1, nx)) for k in ("Ry", "Dy", "wy")})
+    b = _Bound(prob, V, Ax, Ay)
+    rc = lib().orc_faces(b.ref(), _d(out["Rx"]), _d(out["Ry"]), _d(out["Dx"]), _d(out["Dy"]),
+                         _d(out["wx"]), _d(out["wy"]))
+    if rc:
+        raise RuntimeError(f"orc_faces failed ({rc})")
+    return out
+
+
+def _csr(n, rp, cl, vl, nnz):
+    import scipy.sparse as sp
+    return sp.csr_matrix((vl[:nnz].copy(), cl[:nnz].copy(), rp.copy()), shape=(n, n))
+
+
+def assemble_coupled(prob):
+    """Paper-literal coupled system (2N x 2N, interleaved [E_k, T_k]) as scipy CSR, rhs."""
+    N = prob.ncells
+    rp = np.zeros(2 * N + 1, np.int32); cl = np.zeros(8 * N, np.int32)
+    vl = np.zeros(8 * N); rhs = np.zeros(2 * N)
+    b = _Bound(prob)
+    nnz = lib().orc_assemble_coupled(b.ref(), _i(rp), _i(cl), _d(vl), _d(rhs))
+    if nnz < 0:
+        raise RuntimeError(f"orc_assemble_coupled failed ({nnz})")
+    return _csr(2 * N, rp, cl, vl, nnz), rhs
+
+
+def assemble_reduced(prob, V=None, Ax=None, Ay=None):
+    """Schur-reduced symmetric system (N x N, rows times V_k) as scipy CSR, rhs."""
+    N = prob.ncells
+    rp = np.zeros(N + 1, np.int32); cl = np.zeros(5 * N, np.int32)
+    vl = np.zeros(5 * N); rhs = np.zeros(N)
+    b = _Bound(prob, V, Ax, Ay)
+    nnz = lib().orc_assemble_reduced(b.ref(), _i(rp), _i(cl), _d(vl), _d(rhs))
+    if nnz < 0:
+        raise RuntimeError(f"orc_assemble_reduced failed ({nnz})")
+    return _csr(N, rp, cl, vl, nnz), rhs
+
+
+def band_solve(A, rhs) -> np.ndarray:
+    A = A.tocsr()
+    n = A.shape[0]
+    rp = np.ascontiguousarray(A.indptr, dtype=np.int32); cl = np.ascontiguousarray(A.indices, dtype=np.int32)
+    vl = np.ascontiguousarray(A.data, dtype=np.float64)
+    x = np.zeros(n)
+    rc = lib().orc_band_solve(n, _i(rp), _i(cl), _d(vl), _d(np.ascontiguousarray(rhs, dtype=np.float64)), _d(x))
+    if rc:
+        raise RuntimeError(f"orc_band_solve failed ({rc})")
+    return x
+
+
+def pcg(A, rhs, x0, tol=1e-15, maxit=1000000):
+    A = A.tocsr()
+    n = A.shape[0]
+    rp = np.ascontiguousarray(A.indptr, dtype=np.int32); cl = np.ascontiguousarray(A.indices, dtype=np.int32)
+    vl = np.ascontiguousarray(A.data, dtype=np.float64)
+    x = np.array(x0, dtype=np.float64, copy=True)
+    it = ctypes.c_int(0); crit = ctypes.c_double(0.0)
+    rc = lib().orc_pcg(n, _i(rp), _i(cl), _d(vl), _d(np.ascontiguousarray(rhs, dtype=np.float64)), _d(x),
+                       float(tol), int(maxit), ctypes.byref(it), ctypes.byref(crit))
+    return x, it.value, crit.value, rc
+
+
+def step(prob, method: str = "lu", tol: float = 1e-15, V=None, Ax=None, Ay=None) -> dict:
+    """One implicit step.  method 'lu': banded LU on the reduced system; 'cg': Jacobi-PCG on
+    the reduced system to the cell-wise relative residual tol; 'coupled': banded LU on the
+    paper-literal coupled system (accurate only for moderate coupling)."""
+    nx, ny = prob.nx, prob.ny
+    E = np.zeros((ny, nx)); T = np.zeros((ny, nx)); eg = np.zeros((ny, nx))
+    info = np.zeros(5)
+    Fx = np.zeros((ny, nx + 1)); Fy = np.zeros((ny + 1, nx))
+    b = _Bound(prob, V, Ax, Ay)
+    m = {"lu": 0, "cg": 1, "coupled": 2}[method]
+    rc = lib().orc_step(b.ref(), m, float(tol), _d(E), _d(T), _d(eg), _d(info), _d(Fx), _d(Fy))
+    if rc < 0:
+        raise RuntimeError(f"orc_step failed ({rc})")
+    return {"E_r": E, "T_g": T, "e_g": eg, "iterations": int(info[0]), "cell_residual": info[1],
+            "l2_residual": info[2], "energy_before": info[3], "energy_after": info[4],
+            "Fx": Fx, "Fy": Fy, "status": rc}
