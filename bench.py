@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 implicit FLD radiation step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload c2|c1|c0] [--rtol R]
+
+A step is one implicit FLD step (coefficients, opacities, limiter, reduced 5-point
+system, Krylov solve, back-substitution, energy sums) over the whole grid.  The default
+workload is the 2048 (r) x 1024 (theta) spherical-polar grid in mixed precision (FP32
+inner PCG, FP64 refinement).  Rank 0 prints one JSON line.
+
+Timing: W untimed warm-up steps, then K steps bracketed by a barrier and a device
+synchronisation; each step is timed with CUDA events on the launching stream.  Before
+every step the inputs are restored from a pristine copy and L2 is flushed (a 512 MiB
+write); both happen outside the per-step events.
+
+--impl reference times the FP64 CPU oracle (plain C, one host core) on a bounded
+sample of the same workload: the full assembly plus a fixed number of CG iterations,
+extrapolated to the iteration count of the FP64 Jacobi-PCG at the same tolerance.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FLD cell-updates/s at 1e-8 rel residual (FP32+refine vs FP64 GPU); p99 latency"
+UNIT = "cell-updates/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM = 6800.0
+
+# algorithmic bytes per cell (each array touched once per pass)
+BYTES_ITER = {1: 32.0, 0: 64.0}       # 2 coefficients + (x, r, p) read and written
+BYTES_RESID = {1: 60.0, 0: 40.0}      # FP64 residual (c_W, c_S, b, y in; r out) [+ y += d for mixed]
+KERNELS_PER_STEP = 7                  # cells, faces, diag, scale, pcg, backsub, finalize
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["c2", "c1", "c0"], default="c2")
+    ap.add_argument("--rtol", type=float, default=None)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison path")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_2602_12545_gb300 import workloads as W
+    P = {"c0": W.config0, "c1": W.config1, "c2": W.config2}[name]()
+    desc = {"c0": "64x64 uniform Cartesian, reflecting, dt=1e4 s",
+            "c1": "1024x1024 Cartesian, dx geometric x1.002, Milne at +x, dt=1e5 s",
+            "c2": "2048 (r, log 1e11-1e14 cm) x 1024 (theta 0-pi) spherical-polar, Milne at outer r, dt=1e4 s"}[name]
+    return P, desc
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx = max(mx, float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_index(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids) and ids[local_rank].isdigit():
+            return int(ids[local_rank])
+    return local_rank
+
+
+def traffic_from_profile(kernel_tag, src_hash):
+    """Per-launch DRAM bytes of the solve kernel from a committed ncu summary, if that
+    summary was taken on the current kernel source (same hash), else None."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("source_sha256") != src_hash:
+            return None
+        return float(d["dram_bytes_per_launch_full_size"])
+    except Exception:
+        return None
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("gq_pcg.cu", "gq_device.cuh", "gq_internal.h"):
+        with open(os.path.join(ROOT, "paper_2602_12545_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(P, iters_needed, cg_iters=60):
+    import numpy as np
+    import oracle
+    t0 = time.perf_counter()
+    A, b = oracle.assemble_reduced(P)
+    t1 = time.perf_counter()
+    _, it, _, _ = oracle.pcg(A, b, P.E_r.ravel().copy(), tol=0.0, maxit=cg_iters)
+    t2 = time.perf_counter()
+    t_iter = (t2 - t1) / max(it, 1)
+    t_step = (t1 - t0) + iters_needed * t_iter
+    return {"value": P.ncells / t_step, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"oracle assembly of the full {P.nx}x{P.ny} reduced system plus {it} Jacobi-PCG "
+                       f"iterations on it, extrapolated to {iters_needed} iterations (the FP64 Jacobi-PCG "
+                       f"count at the same tolerance); single host thread"),
+            "t_assembly_s": t1 - t0, "t_per_iteration_s": t_iter}, t2 - t0
+
+
+# ---------------------------------------------------------------------------
+# our implementation
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2602_12545_gb300 import fld as F
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    P, desc = workload(args.workload)
+    rtol = args.rtol if args.rtol is not None else (1e-8 if args.workload == "c2" else P.rtol)
+    prec = 1 if args.workload == "c2" else P.precision
+    plan = F.FLDPlan.for_problem(P)
+    rho0, eg0, E0, _ = F.device_fields(P)
+    rho = rho0
+    e_g, E, T = eg0.clone(), E0.clone(), torch.empty_like(E0)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def one(opts):
+        e_g.copy_(eg0)
+        E.copy_(E0)
+        flush.fill_(1.0)
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        info = plan.step(rho, e_g, E, T, opacity_R=P.opacity_R, opacity_P=P.opacity_P, gamma=P.gamma, mu=P.mu,
+                         dt=P.dt, bc=P.bc, opts=opts)
+        s1.record(stream)
+        s1.synchronize()
+        info["ms"] = s0.elapsed_time(s1)
+        return info
+
+    opts = F.SolverOptions(prec=prec, limiter=P.limiter, rtol=rtol, timing=1)
+    # accuracy reference: FP64 path solved tightly (untimed)
+    ref_opts = F.SolverOptions(prec=0, limiter=P.limiter, rtol=1e-13, timing=0, max_iter=1000000)
+    one(ref_opts)
+    E_ref, T_ref = E.clone(), T.clone()
+
+    for _ in range(args.warmup):
+        one(opts)
+
+    clocks = Clocks(gpu_index(local))
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    infos = [one(opts) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    barrier()
+    ck = clocks.stop()
+    err_E = float(((E - E_ref).abs() / E_ref.abs()).max())
+    err_T = float(((T - T_ref).abs() / T_ref.abs()).max())
+
+    total_ms = sum(i["ms"] for i in infos)
+    if world > 1:
+        tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    N = P.ncells
+    value = world * N * args.steps / (total_ms / 1e3)
+    lat = sorted(i["ms"] for i in infos)
+    p50 = statistics.median(lat)
+    p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
+    its = statistics.mean(i["iterations"] for i in infos)
+    refs = statistics.mean(i["refinements"] for i in infos)
+    t_solve = statistics.mean(i["t_solve_ms"] for i in infos)
+    t_setup = statistics.mean(i["t_setup_ms"] for i in infos)
+    t_finish = statistics.mean(i["t_finish_ms"] for i in infos)
+    alg_bytes = N * (its * BYTES_ITER[prec] + (refs + 1) * BYTES_RESID[prec])
+    achieved = alg_bytes / (t_solve / 1e3) / 1e9
+    peak, peak_kind = peaks()
+    tag = "pcg_mixed_c2" if (prec == 1 and args.workload == "c2") else f"pcg_{'mixed' if prec else 'fp64'}_{args.workload}"
+    traffic = traffic_from_profile(tag, kernel_source_hash())
+    if traffic is not None:
+        traffic = traffic
+
+    # FP64 GPU path on the same workload and tolerance
+    fp64 = None
+    if not args.no_fp64 and prec == 1:
+        f_opts = F.SolverOptions(prec=0, limiter=P.limiter, rtol=rtol, timing=1)
+        one(f_opts)
+        f_infos = [one(f_opts) for _ in range(max(1, min(args.steps, 3)))]
+        f_ms = statistics.mean(i["ms"] for i in f_infos)
+        f_err = float(((E - E_ref).abs() / E_ref.abs()).max())
+        fp64 = {"value": N / (f_ms / 1e3), "unit": UNIT, "ms_per_step": f_ms,
+                "iterations": statistics.mean(i["iterations"] for i in f_infos),
+                "max_rel_err_E_vs_fp64_tight": f_err, "steps": len(f_infos)}
+
+    # end to end: pinned host inputs -> device, step, results -> host, every step
+    e2e = None
+    if not args.no_e2e:
+        h_rho = rho0.cpu().pin_memory()
+        h_eg = eg0.cpu().pin_memory()
+        h_E = E0.cpu().pin_memory()
+        o_E, o_eg, o_T = (torch.empty_like(h_E).pin_memory() for _ in range(3))
+        d_rho = torch.empty_like(rho0)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n_e2e = max(1, min(args.steps, 3))
+        for _ in range(n_e2e):
+            d_rho.copy_(h_rho, non_blocking=True)
+            e_g.copy_(h_eg, non_blocking=True)
+            E.copy_(h_E, non_blocking=True)
+            plan.step(d_rho, e_g, E, T, opacity_R=P.opacity_R, opacity_P=P.opacity_P, gamma=P.gamma, mu=P.mu,
+                      dt=P.dt, bc=P.bc, opts=opts)
+            o_E.copy_(E, non_blocking=True)
+            o_eg.copy_(e_g, non_blocking=True)
+            o_T.copy_(T, non_blocking=True)
+            torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        barrier()
+        e2e = {"value": world * N * n_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 3 * 8 * N,
+               "d2h_bytes_per_step": 3 * 8 * N, "steps": n_e2e}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        it_fp64 = int(fp64["iterations"]) if fp64 else int(its)
+        cpu, _ = oracle_sample(P, it_fp64)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == 1 else "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{P.name}_{'mixed' if prec else 'fp64'}", "grid": desc, "nx": P.nx, "ny": P.ny,
+                   "cells": N, "precision": "FP32 inner PCG + FP64 refinement" if prec else "FP64 PCG",
+                   "rtol": rtol, "residual": "cell-wise max |b-Ax|_k/(A_kk x_k) of the reduced system",
+                   "l2": "inputs restored and L2 flushed (512 MiB write) before every step, outside the timed events",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "step_latency_ms": {"p50": p50, "p99": p99},
+        "solver": {"iterations": its, "refinements": refs, "rel_residual": infos[-1]["rel_residual"],
+                   "rel_residual_l2": infos[-1]["rel_residual_l2"], "max_rel_err_E_vs_fp64_tight": err_E,
+                   "max_rel_err_T_vs_fp64_tight": err_T, "t_setup_ms": t_setup, "t_solve_ms": t_solve,
+                   "t_finish_ms": t_finish, "solve_blocks": infos[-1]["solve_blocks"]},
+        "roofline": {"kernel": "k_pcg (persistent cooperative Krylov solve)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": peak_kind, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "bytes_per_cell": {"iteration": BYTES_ITER[prec], "fp64_residual": BYTES_RESID[prec]}},
+        "fp64_gpu": fp64,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "clocks": ck,
+        "wall_s_timed_loop": t_wall,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The FP64 CPU oracle on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    P, desc = workload(args.workload)
+    rtol = args.rtol if args.rtol is not None else (1e-8 if args.workload == "c2" else P.rtol)
+    iters = {"c0": 148, "c1": 1264, "c2": 4500}[args.workload]
+    for _ in range(args.warmup):
+        oracle_sample(P, iters, cg_iters=10)
+    samples = []
+    for _ in range(args.steps):
+        s, _ = oracle_sample(P, iters, cg_iters=30)
+        samples.append(s)
+    v = statistics.mean(s["value"] for s in samples)
+    ms = P.ncells / v * 1e3
+    cpu = dict(samples[-1])
+    cpu["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{P.name}_{'mixed' if args.workload == 'c2' else 'fp64'}", "grid": desc,
+                       "nx": P.nx, "ny": P.ny, "cells": P.ncells, "rtol": rtol,
+                       "iterations_assumed": iters},
+            "cpu_baseline": cpu,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,167 @@
+/*
+ * gq_fld.h -- C ABI of the GB300 implicit flux-limited-diffusion (FLD) radiation step.
+ *
+ * The operation is the radiation / gas-thermodynamics sub-step of Chen & Bai, "Guangqi:
+ * a two-dimensional radiation hydrodynamic code with realistic equations of state"
+ * (arXiv 2602.12545), Sec. 3.2: one backward-Euler step of
+ *     dE/dt - div(D grad E) = -G0,   C_V dT/dt = G0,   G0 = rho c kappa_P E - eta,
+ * eta = kappa_P rho c a T^4 (Sec. 2), with the flux-limited diffusion coefficient
+ * D = c lambda(R) / (kappa_R rho) (Sec. 2, Eqs. limiter and reducer; face values per
+ * Eq. diffcoeff), the linearisation (T^{n+1})^4 ~ 4 T^3 T^{n+1} - 3 T^4 (Sec. 3.2.1), the
+ * coefficients phi_1..phi_11, psi_5, psi_6, psi_11 (Eqs. phi1-psi7, alpha, fldg) and the
+ * coupled linear system of Eqs. linearsys1-2, which is reduced exactly to a symmetric
+ * positive-definite 5-point system in E and solved by a preconditioned Krylov method to a
+ * relative residual (Eq. linearsystem).
+ *
+ * Conventions shared by every entry point
+ *   - Cell arrays are row-major [ny][nx], x (or r) fastest, float64, in DEVICE memory
+ *     owned by the caller, unless a parameter says "host".
+ *   - Units are CGS.  Boundary sides are ordered -x, +x, -y, +y (r-, r+, theta-, theta+).
+ *   - Every call returns a gq_status and never aborts.  Work is enqueued on the given CUDA
+ *     stream (a cudaStream_t passed as void*, NULL = legacy default stream); where a call
+ *     fills a host result struct, it has synchronised with that stream before returning.
+ *   - A plan is used by one host thread at a time.
+ */
+#ifndef GQ_FLD_H
+#define GQ_FLD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GQ_OK = 0,
+    GQ_ERR_INVALID_ARG = 1,     /* bad pointer, size, option or non-positive field value */
+    GQ_ERR_CUDA = 2,            /* a CUDA runtime call failed */
+    GQ_ERR_OOM = 3,             /* device allocation failed */
+    GQ_ERR_NOT_CONVERGED = 4,   /* max_iter reached; the best iterate is written */
+    GQ_ERR_NONFINITE = 5,       /* NaN / Inf in the inputs or in a solver reduction */
+    GQ_ERR_TIMEOUT = 6,         /* an inter-block wait exceeded its spin limit */
+    GQ_ERR_BUDGET = 7           /* serving: request does not fit the memory budget */
+} gq_status;
+
+enum { GQ_CARTESIAN = 0, GQ_SPHERICAL_POLAR = 1 };
+enum { GQ_BC_REFLECT = 0, GQ_BC_OUTFLOW_MILNE = 1 };
+enum { GQ_LIMITER_LP = 0, GQ_LIMITER_MINERBO = 1, GQ_LIMITER_NONE = 2 };
+enum { GQ_PREC_FP64 = 0, GQ_PREC_MIXED = 1 };
+
+/* Grid geometry (Sec. 3.2.1 and Eq. fldg).  Cartesian (x, y) per unit depth, or
+ * axisymmetric spherical-polar (r, theta) with the common factor 2 pi dropped.
+ * x_faces: host, nx+1 strictly increasing face coordinates (x or r > 0).
+ * y_faces: host, ny+1 strictly increasing (y, or theta in [0, pi]).
+ * area_x [ny][nx+1], area_y [ny+1][nx], volume [ny][nx]: optional host arrays that
+ * replace the derived face areas dS and volumes dV; NULL derives them from the faces. */
+typedef struct {
+    int nx, ny;
+    int coord;                       /* GQ_CARTESIAN or GQ_SPHERICAL_POLAR */
+    const double *x_faces, *y_faces;
+    const double *area_x, *area_y, *volume;
+} gq_grid_desc;
+
+/* Mean opacities as power laws kappa = k0 + k1 rho^a T^b (cm^2/g) at T = T_g^n
+ * (Sec. 2 defines kappa_R and kappa_P; the paper tabulates them, a power law stands in). */
+typedef struct { double k0_R, k1_R, a_R, b_R, k0_P, k1_P, a_P, b_P; } gq_opacity_law;
+
+/* Ideal gas: e_g = C_V T with C_V = rho k_B / ((gamma - 1) mu m_H) (Sec. 3.2, C_V = de/dT). */
+typedef struct { double gamma, mu; } gq_eos;
+
+/* Per-side boundary kind: GQ_BC_REFLECT (no flux) or GQ_BC_OUTFLOW_MILNE (Eq. milne). */
+typedef struct { int side[4]; } gq_bc;
+
+/* Solver options.
+ *   prec        GQ_PREC_FP64: FP64 Jacobi-PCG.  GQ_PREC_MIXED: FP32 Jacobi-PCG inside FP64
+ *               iterative refinement (the FP64 residual b - A x is recomputed whenever the
+ *               FP32 residual has fallen by inner_rtol, keeping the search direction).
+ *   limiter     GQ_LIMITER_LP (Levermore-Pomraning rational form), _MINERBO (Eq. limiter),
+ *               _NONE (lambda = 1/3).
+ *   rtol        stop when max_k |b - A x|_k / (A_kk |x_k|) <= rtol (the cell-wise relative
+ *               residual of the reduced system; the paper's 2-norm form of Eq. linearsystem
+ *               is reported in gq_step_info.rel_residual_l2).
+ *   max_iter    cap on Krylov iterations (> 0).
+ *   inner_rtol  mixed only: FP32 residual drop that triggers an FP64 refinement, in (0, 1).
+ *   max_refine  cap on FP64 residual evaluations after the first (> 0).  Independently,
+ *               the solve ends with GQ_ERR_NOT_CONVERGED when six consecutive FP64
+ *               residuals fail to improve the best one by 10% (rtol below the FP64
+ *               rounding floor of the cell-wise residual).
+ *   spin_limit  cap on the polling iterations of any inter-block wait (0 = default, about
+ *               a second); exceeding it ends the solve with GQ_ERR_TIMEOUT.
+ *   restart     mixed only: 1 restarts the Krylov space at every refinement (classical
+ *               iterative refinement), 0 keeps the search direction (default).
+ *   timing      1 records CUDA events around the set-up, solve and finish phases on the
+ *               stream and reports their durations in gq_step_info (0 = off). */
+typedef struct {
+    int prec;
+    int limiter;
+    double rtol;
+    int max_iter;
+    double inner_rtol;
+    int max_refine;
+    int64_t spin_limit;
+    int restart;
+    int timing;
+    int reserved[6];
+} gq_solver_opts;
+
+/* Result of one step (host struct). */
+typedef struct {
+    int iterations;             /* Krylov iterations (FP32 ones for the mixed path) */
+    int refinements;            /* FP64 residual evaluations after the initial one */
+    double rel_residual;        /* final cell-wise relative residual (see rtol) */
+    double rel_residual_l2;     /* |b - A x|_2 / |b|_2 of the reduced system (Eq. linearsystem) */
+    double energy_before;       /* sum_k V_k (E_k + e_g,k) at time n (axisymmetric: / 2 pi) */
+    double energy_after;        /* the same at time n+1 */
+    int status;                 /* gq_status of the step */
+    int solve_blocks;           /* blocks of the cooperative solve launch */
+    double t_setup_ms;          /* with opts.timing: set-up kernels (coefficients, scaling) */
+    double t_solve_ms;          /* with opts.timing: the Krylov solve kernel */
+    double t_finish_ms;         /* with opts.timing: back-substitution and energy sums */
+    int reserved[4];
+} gq_step_info;
+
+typedef struct gq_fld_plan gq_fld_plan;
+
+/* Build a plan for one grid: validates the geometry, computes volumes, face areas,
+ * volume centres and centre distances in FP64 on the host (Eqs. fldg and alpha), uploads
+ * them and allocates the device workspace of one step.  The plan owns that memory until
+ * gq_fld_destroy.  Errors: GQ_ERR_INVALID_ARG (nx or ny < 1, NULL faces, non-increasing
+ * faces, theta outside [0, pi], r <= 0), GQ_ERR_OOM, GQ_ERR_CUDA.  *out is NULL on error. */
+gq_status gq_fld_setup(const gq_grid_desc *grid, gq_fld_plan **out);
+
+/* Device bytes held by a plan (geometry and workspace). */
+size_t gq_fld_plan_bytes(const gq_fld_plan *plan);
+
+/* One implicit FLD step (Sec. 3.2.1, a single sub-cycle, n_sub = 1): face coefficients,
+ * C_V, the phi / psi coefficients, the reduced system, its Krylov solve and T^{n+1}.
+ *   rho      [ny][nx] device, g/cm^3, > 0, read only.
+ *   e_g      [ny][nx] device, erg/cm^3, > 0, in: e_g^n, out: e_g^{n+1}.
+ *   E_r      [ny][nx] device, erg/cm^3, > 0, in: E^n, out: E^{n+1}.
+ *   T_g_out  [ny][nx] device, K, out: T_g^{n+1} (may be NULL).
+ *   opacity, eos, bc, opts: host structs.  dt > 0 (s).
+ *   info     host, filled on return (may be NULL).
+ * e_g and E_r are written only when the step returns GQ_OK or GQ_ERR_NOT_CONVERGED.
+ * Errors: GQ_ERR_INVALID_ARG (arguments, or a field value <= 0), GQ_ERR_NONFINITE,
+ * GQ_ERR_NOT_CONVERGED, GQ_ERR_TIMEOUT, GQ_ERR_CUDA. */
+gq_status gq_fld_step(gq_fld_plan *plan, const double *rho, double *e_g, double *E_r, double *T_g_out,
+                      const gq_opacity_law *opacity, const gq_eos *eos, double dt, const gq_bc *bc,
+                      const gq_solver_opts *opts, void *stream, gq_step_info *info);
+
+/* Release a plan and its device memory (NULL is ignored). */
+void gq_fld_destroy(gq_fld_plan *plan);
+
+/* Default solver options: FP64, LP limiter, rtol 1e-10, max_iter 200000, inner_rtol 0.1,
+ * max_refine 200, default spin limit, keep the search direction. */
+void gq_solver_opts_default(gq_solver_opts *opts);
+
+/* Static description of a status code. */
+const char *gq_status_string(gq_status status);
+
+/* Library version "major.minor.patch". */
+const char *gq_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GQ_FLD_H */

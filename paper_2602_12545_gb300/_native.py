@@ -1,0 +1,104 @@
+"""ctypes declarations of the C ABI in include/gq_fld.h and the library loader.
+
+The CUDA library is required: there is no fallback.  Loading fails with a clear error
+when libgqfld.so has not been built (``python -m paper_2602_12545_gb300.build``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgqfld.so")
+
+GQ_OK = 0
+GQ_ERR_INVALID_ARG = 1
+GQ_ERR_CUDA = 2
+GQ_ERR_OOM = 3
+GQ_ERR_NOT_CONVERGED = 4
+GQ_ERR_NONFINITE = 5
+GQ_ERR_TIMEOUT = 6
+GQ_ERR_BUDGET = 7
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("coord", ctypes.c_int),
+                ("x_faces", _dp), ("y_faces", _dp), ("area_x", _dp), ("area_y", _dp), ("volume", _dp)]
+
+
+class OpacityLaw(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("k0_R", "k1_R", "a_R", "b_R", "k0_P", "k1_P", "a_P", "b_P")]
+
+
+class Eos(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("mu", ctypes.c_double)]
+
+
+class Bc(ctypes.Structure):
+    _fields_ = [("side", ctypes.c_int * 4)]
+
+
+class SolverOpts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("limiter", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("inner_rtol", ctypes.c_double), ("max_refine", ctypes.c_int),
+                ("spin_limit", ctypes.c_int64), ("restart", ctypes.c_int), ("timing", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
+
+
+class StepInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("refinements", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("rel_residual_l2", ctypes.c_double), ("energy_before", ctypes.c_double),
+                ("energy_after", ctypes.c_double), ("status", ctypes.c_int), ("solve_blocks", ctypes.c_int),
+                ("t_setup_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double), ("t_finish_ms", ctypes.c_double),
+                ("reserved", ctypes.c_int * 4)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+# every symbol include/gq_fld.h declares, with (restype, argtypes)
+SIGNATURES = {
+    "gq_fld_setup": (ctypes.c_int, [ctypes.POINTER(GridDesc), ctypes.POINTER(ctypes.c_void_p)]),
+    "gq_fld_plan_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "gq_fld_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.POINTER(OpacityLaw), ctypes.POINTER(Eos),
+                                   ctypes.c_double, ctypes.POINTER(Bc), ctypes.POINTER(SolverOpts),
+                                   ctypes.c_void_p, ctypes.POINTER(StepInfo)]),
+    "gq_fld_destroy": (None, [ctypes.c_void_p]),
+    "gq_solver_opts_default": (None, [ctypes.POINTER(SolverOpts)]),
+    "gq_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "gq_version": (ctypes.c_char_p, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libgqfld.so and declare its signatures (raises if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library not built: {path} is missing "
+                                   "(run `python -m paper_2602_12545_gb300.build`)")
+            L = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def status_string(code: int) -> str:
+    return load().gq_status_string(int(code)).decode()
+
+
+class GQError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = int(code)
+        super().__init__(f"{where}: {status_string(code)} (status {code})")

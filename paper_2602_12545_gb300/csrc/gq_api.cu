@@ -1,0 +1,419 @@
+// C ABI of the GB300 implicit FLD step: plans (geometry + workspace) and the step call.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "gq_device.cuh"
+#include "gq_internal.h"
+
+struct gq_fld_plan {
+    int nx, ny, N, coord;
+    int device;
+    int num_sms;
+    int solve_grid_max;     // co-resident blocks of the solve kernel
+    int setup_blocks;
+    void* arena;
+    size_t arena_bytes;
+    gq::DeviceGeometry geo;
+    gq::Workspace ws;
+    gq::SolveCtl* ctl_host;  // pinned
+    cudaEvent_t ev[4];       // phase timing
+};
+
+namespace {
+
+constexpr int64_t kDefaultSpin = 1ll << 24;
+
+// ---------------------------------------------------------------------------
+// host geometry (FP64): volumes, face areas, volume centres, centre distances
+// ---------------------------------------------------------------------------
+
+// int_{v}^{v+h} (t - v) sin t dt and int_v^{v+h} sin t dt, evaluated without
+// cancellation for small h (series in h for the two h-only factors).
+void theta_moments(double v, double h, double* first, double* zeroth) {
+    double A, B;   // A = cos h + h sin h - 1, B = sin h - h cos h
+    if (h < 0.05) {
+        const double h2 = h * h;
+        A = h2 * (0.5 + h2 * (-1.0 / 8.0 + h2 * (1.0 / 144.0 + h2 * (-1.0 / 5760.0))));
+        B = h2 * h * (1.0 / 3.0 + h2 * (-1.0 / 30.0 + h2 * (1.0 / 840.0 + h2 * (-1.0 / 45360.0))));
+    } else {
+        A = std::cos(h) + h * std::sin(h) - 1.0;
+        B = std::sin(h) - h * std::cos(h);
+    }
+    const double sv = std::sin(v), cv = std::cos(v);
+    const double half = std::sin(0.5 * h);
+    *first = sv * A + cv * B;
+    *zeroth = sv * std::sin(h) + cv * 2.0 * half * half;
+}
+
+struct HostGeometry {
+    std::vector<double> V, gx, gy, dxf, thx, ymet, dyf, thy;
+};
+
+gq_status build_geometry(const gq_grid_desc* gd, HostGeometry& H) {
+    const int nx = gd->nx, ny = gd->ny;
+    const double* xf = gd->x_faces;
+    const double* yf = gd->y_faces;
+    for (int i = 0; i <= nx; i++)
+        if (!std::isfinite(xf[i]) || (i > 0 && !(xf[i] > xf[i - 1]))) return GQ_ERR_INVALID_ARG;
+    for (int j = 0; j <= ny; j++)
+        if (!std::isfinite(yf[j]) || (j > 0 && !(yf[j] > yf[j - 1]))) return GQ_ERR_INVALID_ARG;
+    const bool sph = gd->coord == GQ_SPHERICAL_POLAR;
+    if (sph && (!(xf[0] > 0.0) || yf[0] < 0.0 || yf[ny] > M_PI + 1e-12)) return GQ_ERR_INVALID_ARG;
+
+    std::vector<double> xc(nx), yc(ny), dcos(ny);
+    if (!sph) {
+        for (int i = 0; i < nx; i++) xc[i] = 0.5 * (xf[i] + xf[i + 1]);
+        for (int j = 0; j < ny; j++) yc[j] = 0.5 * (yf[j] + yf[j + 1]);
+    } else {
+        for (int i = 0; i < nx; i++) {
+            const double a = xf[i], b = xf[i + 1];
+            // int r^3 dr / int r^2 dr over [a, b]
+            xc[i] = 0.75 * (a + b) * (a * a + b * b) / (a * a + a * b + b * b);
+        }
+        for (int j = 0; j < ny; j++) {
+            double m1, m0;
+            theta_moments(yf[j], yf[j + 1] - yf[j], &m1, &m0);
+            yc[j] = yf[j] + m1 / m0;
+            dcos[j] = m0;
+        }
+    }
+    const size_t N = (size_t)nx * ny;
+    H.V.assign(N, 0.0);
+    std::vector<double> Ax((size_t)ny * (nx + 1)), Ay((size_t)(ny + 1) * nx);
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            const double a = xf[i], b = xf[i + 1];
+            H.V[(size_t)j * nx + i] = sph ? (b - a) * (a * a + a * b + b * b) / 3.0 * dcos[j]
+                                          : (b - a) * (yf[j + 1] - yf[j]);
+        }
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i <= nx; i++)
+            Ax[(size_t)j * (nx + 1) + i] = sph ? xf[i] * xf[i] * dcos[j] : yf[j + 1] - yf[j];
+    for (int j = 0; j <= ny; j++) {
+        double sf = 1.0;
+        if (sph) sf = (yf[j] <= 0.0 || yf[j] >= M_PI) ? 0.0 : std::sin(yf[j]);
+        for (int i = 0; i < nx; i++) {
+            const double a = xf[i], b = xf[i + 1];
+            Ay[(size_t)j * nx + i] = sph ? sf * (b - a) * (b + a) * 0.5 : b - a;
+        }
+    }
+    if (gd->volume) std::memcpy(H.V.data(), gd->volume, sizeof(double) * N);
+    if (gd->area_x) std::memcpy(Ax.data(), gd->area_x, sizeof(double) * Ax.size());
+    if (gd->area_y) std::memcpy(Ay.data(), gd->area_y, sizeof(double) * Ay.size());
+    for (double v : H.V)
+        if (!(v > 0.0) || !std::isfinite(v)) return GQ_ERR_INVALID_ARG;
+
+    H.dxf.assign(nx + 1, 0.0);
+    H.thx.assign(nx + 1, 0.0);
+    H.dyf.assign(ny + 1, 0.0);
+    H.thy.assign(ny + 1, 0.0);
+    H.ymet.assign(nx, 1.0);
+    if (sph)
+        for (int i = 0; i < nx; i++) H.ymet[i] = xc[i];
+    for (int i = 1; i < nx; i++) {
+        H.dxf[i] = xc[i] - xc[i - 1];
+        H.thx[i] = (xf[i] - xc[i - 1]) / (xc[i] - xc[i - 1]);
+    }
+    H.dxf[0] = xc[0] - xf[0];
+    H.dxf[nx] = xf[nx] - xc[nx - 1];
+    for (int j = 1; j < ny; j++) {
+        H.dyf[j] = yc[j] - yc[j - 1];
+        H.thy[j] = (yf[j] - yc[j - 1]) / (yc[j] - yc[j - 1]);
+    }
+    H.dyf[0] = yc[0] - yf[0];
+    H.dyf[ny] = yf[ny] - yc[ny - 1];
+    H.gx.assign(Ax.size(), 0.0);
+    H.gy.assign(Ay.size(), 0.0);
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i <= nx; i++) H.gx[(size_t)j * (nx + 1) + i] = Ax[(size_t)j * (nx + 1) + i] / H.dxf[i];
+    for (int j = 0; j <= ny; j++)
+        for (int i = 0; i < nx; i++)
+            H.gy[(size_t)j * nx + i] = Ay[(size_t)j * nx + i] / (H.ymet[i] * H.dyf[j]);
+    return GQ_OK;
+}
+
+// bump allocator over one device allocation
+struct Bump {
+    char* base;
+    size_t off;
+    template <class T>
+    T* take(size_t n) {
+        off = (off + 255) & ~size_t(255);
+        T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+        off += n * sizeof(T);
+        return p;
+    }
+};
+
+void layout(gq_fld_plan* P, Bump& b) {
+    const size_t N = P->N, nx = P->nx, ny = P->ny;
+    auto& g = P->geo;
+    auto& w = P->ws;
+    g.V = b.take<double>(N);
+    g.gx = b.take<double>(ny * (nx + 1));
+    g.gy = b.take<double>((ny + 1) * nx);
+    g.dxf = b.take<double>(nx + 1);
+    g.thx = b.take<double>(nx + 1);
+    g.ymet = b.take<double>(nx);
+    g.dyf = b.take<double>(ny + 1);
+    g.thy = b.take<double>(ny + 1);
+    w.sig = b.take<double>(N);
+    w.dloc = b.take<double>(N);
+    w.rhs = b.take<double>(N);
+    w.tA = b.take<double>(N);
+    w.tB = b.take<double>(N);
+    w.wW = b.take<double>(N);
+    w.wS = b.take<double>(N);
+    w.wB = b.take<double>(N);
+    w.y = b.take<double>(N);
+    w.r64 = b.take<double>(N);
+    w.p64[0] = b.take<double>(N);
+    w.p64[1] = b.take<double>(N);
+    w.q64 = b.take<double>(N);
+    w.cW32 = b.take<float>(N);
+    w.cS32 = b.take<float>(N);
+    w.d32 = b.take<float>(N);
+    w.r32 = b.take<float>(N);
+    w.p32[0] = b.take<float>(N);
+    w.p32[1] = b.take<float>(N);
+    w.q32 = b.take<float>(N);
+    w.partials = b.take<double>(2 * (size_t)P->solve_grid_max * gq::kSlots);
+    w.epart = b.take<double>(2 * (size_t)P->setup_blocks);
+    w.bar = b.take<unsigned>(2);
+    w.ctl = b.take<gq::SolveCtl>(1);
+}
+
+bool finite_all(const double* v, int n) {
+    for (int i = 0; i < n; i++)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gq_version(void) { return "0.1.0"; }
+
+const char* gq_status_string(gq_status s) {
+    switch (s) {
+        case GQ_OK: return "ok";
+        case GQ_ERR_INVALID_ARG: return "invalid argument";
+        case GQ_ERR_CUDA: return "CUDA error";
+        case GQ_ERR_OOM: return "out of device memory";
+        case GQ_ERR_NOT_CONVERGED: return "solver did not converge";
+        case GQ_ERR_NONFINITE: return "non-finite value";
+        case GQ_ERR_TIMEOUT: return "inter-block wait timed out";
+        case GQ_ERR_BUDGET: return "memory budget exceeded";
+    }
+    return "unknown status";
+}
+
+void gq_solver_opts_default(gq_solver_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->prec = GQ_PREC_FP64;
+    o->limiter = GQ_LIMITER_LP;
+    o->rtol = 1e-10;
+    o->max_iter = 200000;
+    o->inner_rtol = 0.1;
+    o->max_refine = 200;
+    o->spin_limit = 0;
+    o->restart = 0;
+}
+
+gq_status gq_fld_setup(const gq_grid_desc* gd, gq_fld_plan** out) {
+    if (!out) return GQ_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!gd || !gd->x_faces || !gd->y_faces || gd->nx < 1 || gd->ny < 1) return GQ_ERR_INVALID_ARG;
+    if (gd->coord != GQ_CARTESIAN && gd->coord != GQ_SPHERICAL_POLAR) return GQ_ERR_INVALID_ARG;
+    if ((long long)gd->nx * gd->ny > (1ll << 30)) return GQ_ERR_INVALID_ARG;
+    HostGeometry H;
+    gq_status st = build_geometry(gd, H);
+    if (st != GQ_OK) return st;
+
+    gq_fld_plan* P = new (std::nothrow) gq_fld_plan();
+    if (!P) return GQ_ERR_OOM;
+    P->nx = gd->nx;
+    P->ny = gd->ny;
+    P->N = gd->nx * gd->ny;
+    P->coord = gd->coord;
+    if (cudaGetDevice(&P->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device) != cudaSuccess) {
+        delete P;
+        return GQ_ERR_CUDA;
+    }
+    const int per_sm = gq::solve_max_blocks_per_sm();
+    if (per_sm < 1) { delete P; return GQ_ERR_CUDA; }
+    const int need = (P->N + gq::kSolveThreads - 1) / gq::kSolveThreads;
+    P->solve_grid_max = std::max(1, std::min(per_sm * P->num_sms, need));
+    P->setup_blocks = std::max(1, std::min(P->num_sms * 8, (P->N + gq::kSetupThreads - 1) / gq::kSetupThreads));
+
+    Bump sizing{nullptr, 0};
+    layout(P, sizing);
+    P->arena_bytes = sizing.off + 256;
+    if (cudaMalloc(&P->arena, P->arena_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete P;
+        return GQ_ERR_OOM;
+    }
+    Bump real{static_cast<char*>(P->arena), 0};
+    layout(P, real);
+    if (cudaMallocHost(reinterpret_cast<void**>(&P->ctl_host), sizeof(gq::SolveCtl)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(P->arena);
+        delete P;
+        return GQ_ERR_OOM;
+    }
+    for (int t = 0; t < 4; t++) {
+        if (cudaEventCreate(&P->ev[t]) != cudaSuccess) {
+            cudaGetLastError();
+            gq_fld_destroy(P);
+            return GQ_ERR_CUDA;
+        }
+    }
+    auto up = [](const double* dst, const std::vector<double>& v) {
+        return cudaMemcpy(const_cast<double*>(dst), v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice);
+    };
+    cudaError_t e = cudaSuccess;
+    const auto& g = P->geo;
+    if (e == cudaSuccess) e = up(g.V, H.V);
+    if (e == cudaSuccess) e = up(g.gx, H.gx);
+    if (e == cudaSuccess) e = up(g.gy, H.gy);
+    if (e == cudaSuccess) e = up(g.dxf, H.dxf);
+    if (e == cudaSuccess) e = up(g.thx, H.thx);
+    if (e == cudaSuccess) e = up(g.ymet, H.ymet);
+    if (e == cudaSuccess) e = up(g.dyf, H.dyf);
+    if (e == cudaSuccess) e = up(g.thy, H.thy);
+    if (e != cudaSuccess) {
+        gq_fld_destroy(P);
+        return GQ_ERR_CUDA;
+    }
+    *out = P;
+    return GQ_OK;
+}
+
+size_t gq_fld_plan_bytes(const gq_fld_plan* P) { return P ? P->arena_bytes : 0; }
+
+void gq_fld_destroy(gq_fld_plan* P) {
+    if (!P) return;
+    if (P->arena) cudaFree(P->arena);
+    if (P->ctl_host) cudaFreeHost(P->ctl_host);
+    for (int t = 0; t < 4; t++)
+        if (P->ev[t]) cudaEventDestroy(P->ev[t]);
+    delete P;
+}
+
+gq_status gq_fld_step(gq_fld_plan* P, const double* rho, double* e_g, double* E_r, double* T_g_out,
+                      const gq_opacity_law* op, const gq_eos* eos, double dt, const gq_bc* bc,
+                      const gq_solver_opts* opts_in, void* stream, gq_step_info* info) {
+    if (info) {
+        std::memset(info, 0, sizeof(*info));
+        info->status = GQ_ERR_INVALID_ARG;
+    }
+    if (!P || !rho || !e_g || !E_r || !op || !eos || !bc) return GQ_ERR_INVALID_ARG;
+    gq_solver_opts opts;
+    if (opts_in) opts = *opts_in;
+    else gq_solver_opts_default(&opts);
+    const double kR[4] = {op->k0_R, op->k1_R, op->a_R, op->b_R};
+    const double kP[4] = {op->k0_P, op->k1_P, op->a_P, op->b_P};
+    if (!finite_all(kR, 4) || !finite_all(kP, 4)) return GQ_ERR_INVALID_ARG;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return GQ_ERR_INVALID_ARG;
+    if (!(eos->gamma > 1.0) || !(eos->mu > 0.0) || !std::isfinite(eos->gamma) || !std::isfinite(eos->mu))
+        return GQ_ERR_INVALID_ARG;
+    for (int s = 0; s < 4; s++)
+        if (bc->side[s] != GQ_BC_REFLECT && bc->side[s] != GQ_BC_OUTFLOW_MILNE) return GQ_ERR_INVALID_ARG;
+    if (opts.prec != GQ_PREC_FP64 && opts.prec != GQ_PREC_MIXED) return GQ_ERR_INVALID_ARG;
+    if (opts.limiter < GQ_LIMITER_LP || opts.limiter > GQ_LIMITER_NONE) return GQ_ERR_INVALID_ARG;
+    if (!(opts.rtol > 0.0) || !(opts.rtol < 1.0) || opts.max_iter < 1) return GQ_ERR_INVALID_ARG;
+    if (opts.prec == GQ_PREC_MIXED &&
+        (!(opts.inner_rtol > 0.0) || !(opts.inner_rtol < 1.0) || opts.max_refine < 1))
+        return GQ_ERR_INVALID_ARG;
+    if (opts.spin_limit < 0) return GQ_ERR_INVALID_ARG;
+
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return GQ_ERR_CUDA;
+    if (cur != P->device && cudaSetDevice(P->device) != cudaSuccess) return GQ_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    gq::StepParams sp{};
+    sp.nx = P->nx;
+    sp.ny = P->ny;
+    sp.N = P->N;
+    for (int s = 0; s < 4; s++) sp.bc[s] = bc->side[s];
+    sp.limiter = opts.limiter;
+    sp.mixed = opts.prec == GQ_PREC_MIXED;
+    for (int t = 0; t < 4; t++) {
+        sp.kR[t] = kR[t];
+        sp.kP[t] = kP[t];
+    }
+    sp.cvfac = gq::kKB / ((eos->gamma - 1.0) * eos->mu * gq::kMH);
+    sp.dt = dt;
+    sp.rho = rho;
+    sp.eg = e_g;
+    sp.E = E_r;
+    sp.eg_out = e_g;
+    sp.T_out = T_g_out;
+
+    gq::SolveParams pp{};
+    pp.nx = P->nx;
+    pp.N = P->N;
+    pp.mixed = sp.mixed;
+    pp.restart = opts.restart;
+    pp.max_iter = opts.max_iter;
+    pp.max_refine = opts.max_refine;
+    pp.rtol = opts.rtol;
+    pp.drop = opts.inner_rtol;
+    pp.spin_limit = opts.spin_limit > 0 ? opts.spin_limit : kDefaultSpin;
+
+    const bool timing = opts.timing != 0;
+    cudaError_t e = cudaMemsetAsync(P->ws.ctl, 0, sizeof(gq::SolveCtl), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->ws.bar, 0, 2 * sizeof(unsigned), st);
+    if (e == cudaSuccess && timing) e = cudaEventRecord(P->ev[0], st);
+    if (e == cudaSuccess) e = gq::launch_setup(sp, P->geo, P->ws, P->setup_blocks, st);
+    if (e == cudaSuccess && timing) e = cudaEventRecord(P->ev[1], st);
+    if (e == cudaSuccess) e = gq::launch_solve(pp, P->ws, P->solve_grid_max, st);
+    if (e == cudaSuccess && timing) e = cudaEventRecord(P->ev[2], st);
+    if (e == cudaSuccess) e = gq::launch_backsub(sp, P->geo, P->ws, P->setup_blocks, st);
+    if (e == cudaSuccess && timing) e = cudaEventRecord(P->ev[3], st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(P->ctl_host, P->ws.ctl, sizeof(gq::SolveCtl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (cur != P->device) cudaSetDevice(cur);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (info) info->status = GQ_ERR_CUDA;
+        return GQ_ERR_CUDA;
+    }
+    const gq::SolveCtl& c = *P->ctl_host;
+    gq_status status;
+    if (c.input_flags & 2) status = GQ_ERR_NONFINITE;
+    else if (c.input_flags & 1) status = GQ_ERR_INVALID_ARG;
+    else if (c.abort) status = GQ_ERR_TIMEOUT;
+    else status = static_cast<gq_status>(c.status);
+    if (info) {
+        info->iterations = c.iterations;
+        info->refinements = c.refinements;
+        info->rel_residual = c.crit;
+        info->rel_residual_l2 = c.l2;
+        info->energy_before = c.energy0;
+        info->energy_after = c.energy1;
+        info->status = status;
+        info->solve_blocks = P->solve_grid_max;
+        if (timing) {
+            float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+            cudaEventElapsedTime(&t0, P->ev[0], P->ev[1]);
+            cudaEventElapsedTime(&t1, P->ev[1], P->ev[2]);
+            cudaEventElapsedTime(&t2, P->ev[2], P->ev[3]);
+            info->t_setup_ms = t0;
+            info->t_solve_ms = t1;
+            info->t_finish_ms = t2;
+        }
+    }
+    return status;
+}
+
+}  // extern "C"

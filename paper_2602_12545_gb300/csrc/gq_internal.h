@@ -1,0 +1,93 @@
+// Internal structures of the GB300 FLD library (not part of the C ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/gq_fld.h"
+
+namespace gq {
+
+// Device-resident control block of one solve.  Written by the kernels, copied to the
+// host once per step.
+struct SolveCtl {
+    int status;          // gq_status
+    int iterations;
+    int refinements;
+    int input_flags;     // bit 0: a field value <= 0, bit 1: a non-finite field value
+    double crit;         // cell-wise relative residual of the last FP64 residual
+    double l2;           // |b - A x|_2 / |b|_2 of the reduced system
+    double energy0;      // sum V (E + e_g) before
+    double energy1;      // and after
+    int abort;           // set by a block whose inter-block wait timed out
+    int pad[3];
+};
+
+// Geometry of a plan in device memory (FP64).  Face arrays:
+//   gx [ny][nx+1]  A_f / d_f of x-face i (between cells i-1, i); boundary faces hold A_f / h
+//   gy [ny+1][nx]  the same for y-faces
+// 1-D arrays: dxf[nx+1] centre distance (boundary: half-cell distance h) of x-face i,
+//   thx[nx+1] interpolation weight (x_f - x_{i-1}) / (x_i - x_{i-1}),
+//   ymet[nx] metric of the y direction (1, or r_c for spherical-polar),
+//   dyf[ny+1], thy[ny+1] the y-face analogues (distance in y or theta, before the metric).
+struct DeviceGeometry {
+    const double *V, *gx, *gy, *dxf, *thx, *ymet, *dyf, *thy;
+};
+
+// Workspace of one step in device memory.
+struct Workspace {
+    // setup outputs (FP64); the scaled system overwrites some in place
+    double *sig;     // sigma = kappa_R rho
+    double *dloc;    // V (1 + beta~), later s = diag^{-1/2}
+    double *rhs;     // b, later b^ = s b
+    double *tA, *tB; // T^{n+1} = tA + tB E^{n+1}
+    double *wW, *wS; // interior face weights (west, south), later the scaled c = w s_k s_m
+    double *wB;      // Milne boundary weights of the cell (diagonal only)
+    // solve (FP64 path and the outer FP64 iterate / residual of the mixed path)
+    double *y, *r64, *p64[2], *q64;
+    // solve (FP32 inner path)
+    float *cW32, *cS32, *d32, *r32, *p32[2], *q32;
+    // reductions, barrier, control
+    double *partials;    // [2][max_blocks][kSlots]
+    double *epart;       // [2][max_setup_blocks] energy partial sums (before, after)
+    unsigned *bar;       // [2]
+    SolveCtl *ctl;
+};
+
+constexpr int kSlots = 5;
+constexpr int kSolveThreads = 512;
+constexpr int kSetupThreads = 256;
+
+struct StepParams {
+    int nx, ny, N;
+    int bc[4];
+    int limiter;
+    int mixed;
+    double kR[4], kP[4];
+    double cvfac;        // C_V / rho = k_B / ((gamma - 1) mu m_H)
+    double dt;
+    const double *rho, *eg;
+    double *E;           // in E^n, out E^{n+1}
+    double *eg_out;
+    double *T_out;
+};
+
+struct SolveParams {
+    int nx, N;
+    int mixed;
+    int restart;
+    int max_iter, max_refine;
+    double rtol, drop;
+    long long spin_limit;
+};
+
+// launchers (stream-ordered)
+cudaError_t launch_setup(const StepParams& sp, const DeviceGeometry& g, const Workspace& w,
+                         int setup_blocks, cudaStream_t st);
+cudaError_t launch_solve(const SolveParams& p, const Workspace& w, int grid, cudaStream_t st);
+cudaError_t launch_backsub(const StepParams& sp, const DeviceGeometry& g, const Workspace& w,
+                           int setup_blocks, cudaStream_t st);
+int solve_max_blocks_per_sm();
+
+}  // namespace gq

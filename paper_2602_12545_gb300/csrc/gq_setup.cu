@@ -1,0 +1,205 @@
+// Set-up and back-substitution kernels of the implicit FLD step (FP64).
+//
+// Per cell (Sec. 3.2.1): C_V = rho k_B / ((gamma-1) mu m_H), T = e_g / C_V, power-law
+// kappa_R and kappa_P at T^n, sigma = kappa_R rho, beta = kappa_P rho c dt (kappa_e =
+// kappa_P), q = 4 beta a T^3.  Eliminating T^{n+1} from the psi row (Eqs. phi1-psi7)
+// gives, per unit volume,
+//     diag = 1 + sum_f alpha g D + beta C_V / (C_V + q),
+//     rhs  = E^n + beta a T^4 C_V / (C_V + q),
+//     T^{n+1} = (C_V T^n + 3 beta a T^4 + beta E^{n+1}) / (C_V + q),
+// which are the exact Schur complement of the coupled system written without the
+// subtraction of beta-sized terms.  Rows are multiplied by V, so the off-diagonals are
+// -w_f with w_f = dt A_f D_f / d_f shared by both cells of a face (Eqs. alpha, fldg),
+// and the system is symmetric positive definite.
+#include "gq_device.cuh"
+#include "gq_internal.h"
+
+namespace gq {
+
+namespace {
+
+__device__ __forceinline__ double opacity(const double* k, double rho, double T) {
+    return k[1] != 0.0 ? k[0] + k[1] * pow(rho, k[2]) * pow(T, k[3]) : k[0];
+}
+
+template <int NT>
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double sh[NT / 32];
+    v = warp_reduce<false>(v);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (warp == 0) {
+        t = lane < NT / 32 ? sh[lane] : 0.0;
+        t = warp_reduce<false>(t);
+    }
+    __syncthreads();
+    return t;   // valid in thread 0
+}
+
+// K1a: per-cell coupling coefficients, input validation, energy before the step
+__global__ void __launch_bounds__(kSetupThreads) k_cells(StepParams sp, DeviceGeometry g, Workspace w) {
+    double eloc = 0.0;
+    int flags = 0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < sp.N; k += gridDim.x * blockDim.x) {
+        const double rho = sp.rho[k], e = sp.eg[k], E = sp.E[k];
+        if (!(isfinite(rho) && isfinite(e) && isfinite(E))) flags |= 2;
+        else if (!(rho > 0.0 && e > 0.0 && E > 0.0)) flags |= 1;
+        const double V = g.V[k];
+        const double cv = rho * sp.cvfac;
+        const double T = e / cv;
+        const double kR = opacity(sp.kR, rho, T);
+        const double kP = opacity(sp.kP, rho, T);
+        const double beta = kP * rho * kC * sp.dt;
+        const double aT3 = kARad * T * T * T;
+        const double aT4 = aT3 * T;
+        const double psi6 = cv + 4.0 * beta * aT3;
+        const double f = cv / psi6;
+        w.sig[k] = kR * rho;
+        w.dloc[k] = V * (1.0 + beta * f);
+        w.rhs[k] = V * (E + beta * aT4 * f);
+        w.tA[k] = (e + 3.0 * beta * aT4) / psi6;
+        w.tB[k] = beta / psi6;
+        eloc += V * (E + e);
+    }
+    if (flags) atomicOr(&w.ctl->input_flags, flags);
+    const double t = block_sum<kSetupThreads>(eloc);
+    if (threadIdx.x == 0) w.epart[blockIdx.x] = t;
+}
+
+// weight of an interior face between cells a (lower coordinate) and b
+__device__ __forceinline__ double face_weight(double sa, double sb, double Ea, double Eb, double th,
+                                              double d, double geo, int lim, double dt) {
+    const double sf = sa + th * (sb - sa);
+    const double Ef = Ea + th * (Eb - Ea);
+    const double R = fabs(Eb - Ea) / (d * sf * Ef);
+    const double D = kC * limiter(lim, R) / sf;
+    return dt * geo * D;
+}
+
+// Milne face (Eq. milne): E_b = k/(1+k) E_cell, k = 2 / (3 sigma h), R_b = 3/2,
+// D_b = c lambda(3/2) / sigma; flux D_b (E - E_b)/h = D_b E / (h (1+k)).
+// geo = A / h.
+__device__ __forceinline__ double milne_weight(double s, double h, double geo, int lim, double dt) {
+    const double kk = 2.0 / (3.0 * s * h);
+    const double D = kC * limiter(lim, 1.5) / s;
+    return dt * geo * D / (1.0 + kk);
+}
+
+// K1b: face weights (each cell owns its west and south faces; boundary faces are
+// folded into the cell's diagonal)
+__global__ void __launch_bounds__(kSetupThreads) k_faces(StepParams sp, DeviceGeometry g, Workspace w) {
+    const int nx = sp.nx, ny = sp.ny;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < sp.N; k += gridDim.x * blockDim.x) {
+        const int j = k / nx, i = k - j * nx;
+        const double sk = w.sig[k], Ek = sp.E[k];
+        double ww = 0.0, ws = 0.0, wb = 0.0;
+        if (i > 0)
+            ww = face_weight(w.sig[k - 1], sk, sp.E[k - 1], Ek, g.thx[i], g.dxf[i],
+                             g.gx[j * (nx + 1) + i], sp.limiter, sp.dt);
+        if (j > 0)
+            ws = face_weight(w.sig[k - nx], sk, sp.E[k - nx], Ek, g.thy[j], g.ymet[i] * g.dyf[j],
+                             g.gy[j * nx + i], sp.limiter, sp.dt);
+        if (i == 0 && sp.bc[0] == 1) wb += milne_weight(sk, g.dxf[0], g.gx[j * (nx + 1)], sp.limiter, sp.dt);
+        if (i == nx - 1 && sp.bc[1] == 1)
+            wb += milne_weight(sk, g.dxf[nx], g.gx[j * (nx + 1) + nx], sp.limiter, sp.dt);
+        if (j == 0 && sp.bc[2] == 1) wb += milne_weight(sk, g.ymet[i] * g.dyf[0], g.gy[i], sp.limiter, sp.dt);
+        if (j == ny - 1 && sp.bc[3] == 1)
+            wb += milne_weight(sk, g.ymet[i] * g.dyf[ny], g.gy[ny * nx + i], sp.limiter, sp.dt);
+        w.wW[k] = ww;
+        w.wS[k] = ws;
+        w.wB[k] = wb;
+    }
+}
+
+// K1c: diagonal of the reduced system and its Jacobi scale s = diag^{-1/2} (in place of dloc)
+__global__ void __launch_bounds__(kSetupThreads) k_diag(StepParams sp, Workspace w) {
+    const int nx = sp.nx, ny = sp.ny;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < sp.N; k += gridDim.x * blockDim.x) {
+        const int j = k / nx, i = k - j * nx;
+        double d = w.dloc[k] + w.wB[k] + w.wW[k] + w.wS[k];
+        if (i < nx - 1) d += w.wW[k + 1];
+        if (j < ny - 1) d += w.wS[k + nx];
+        w.dloc[k] = 1.0 / sqrt(d);
+    }
+}
+
+// K1d: scaled system  A^ = S A S (unit diagonal), b^ = S b, y0 = E^n / s; FP32 copies
+__global__ void __launch_bounds__(kSetupThreads) k_scale(StepParams sp, Workspace w) {
+    const int nx = sp.nx;
+    const double* s = w.dloc;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < sp.N; k += gridDim.x * blockDim.x) {
+        const int j = k / nx, i = k - j * nx;
+        const double sk = s[k];
+        const double cw = i > 0 ? w.wW[k] * sk * s[k - 1] : 0.0;
+        const double cs = j > 0 ? w.wS[k] * sk * s[k - nx] : 0.0;
+        w.wW[k] = cw;
+        w.wS[k] = cs;
+        w.rhs[k] *= sk;
+        w.y[k] = sp.E[k] / sk;
+        if (sp.mixed) {
+            w.cW32[k] = static_cast<float>(cw);
+            w.cS32[k] = static_cast<float>(cs);
+        }
+    }
+}
+
+// K6: back-substitution T^{n+1} = tA + tB E^{n+1}, e_g^{n+1} = e_g + C_V (T^{n+1} - T^n),
+// energy after the step
+__global__ void __launch_bounds__(kSetupThreads) k_backsub(StepParams sp, DeviceGeometry g, Workspace w) {
+    const SolveCtl* ctl = w.ctl;
+    const int st = ctl->status;
+    const bool write = (st == kOk || st == kErrNotConverged) && ctl->abort == 0 && ctl->input_flags == 0;
+    double eloc = 0.0;
+    if (write) {
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < sp.N; k += gridDim.x * blockDim.x) {
+            const double En = w.dloc[k] * w.y[k];
+            const double Tn = w.tA[k] + w.tB[k] * En;
+            const double e = sp.eg[k];
+            const double cv = sp.rho[k] * sp.cvfac;
+            const double en = e + cv * (Tn - e / cv);
+            sp.E[k] = En;
+            sp.eg_out[k] = en;
+            if (sp.T_out) sp.T_out[k] = Tn;
+            eloc += g.V[k] * (En + en);
+        }
+    }
+    const double t = block_sum<kSetupThreads>(eloc);
+    if (threadIdx.x == 0) w.epart[gridDim.x + blockIdx.x] = t;
+}
+
+// deterministic final sums of the energy partials
+__global__ void __launch_bounds__(kSetupThreads) k_finalize(Workspace w, int nblk) {
+    double a = 0.0, b = 0.0;
+    for (int t = threadIdx.x; t < nblk; t += blockDim.x) {
+        a += w.epart[t];
+        b += w.epart[nblk + t];
+    }
+    a = block_sum<kSetupThreads>(a);
+    b = block_sum<kSetupThreads>(b);
+    if (threadIdx.x == 0) {
+        w.ctl->energy0 = a;
+        w.ctl->energy1 = b;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_setup(const StepParams& sp, const DeviceGeometry& g, const Workspace& w, int nblk,
+                         cudaStream_t st) {
+    k_cells<<<nblk, kSetupThreads, 0, st>>>(sp, g, w);
+    k_faces<<<nblk, kSetupThreads, 0, st>>>(sp, g, w);
+    k_diag<<<nblk, kSetupThreads, 0, st>>>(sp, w);
+    k_scale<<<nblk, kSetupThreads, 0, st>>>(sp, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backsub(const StepParams& sp, const DeviceGeometry& g, const Workspace& w, int nblk,
+                           cudaStream_t st) {
+    k_backsub<<<nblk, kSetupThreads, 0, st>>>(sp, g, w);
+    k_finalize<<<1, kSetupThreads, 0, st>>>(w, nblk);
+    return cudaGetLastError();
+}
+
+}  // namespace gq

@@ -1,0 +1,142 @@
+"""Python binding of the implicit FLD step: argument marshalling over the C ABI.
+
+Every step of the path runs in the CUDA library (libgqfld.so); this module only
+checks tensors (float64, contiguous, on the plan's CUDA device) and passes raw
+pointers and the current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _native as N
+from .workloads import FLDProblem
+
+
+def _host_ptr(a: Optional[np.ndarray]):
+    if a is None:
+        return ctypes.cast(None, ctypes.POINTER(ctypes.c_double)), None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), a
+
+
+@dataclasses.dataclass
+class SolverOptions:
+    prec: int = 0                 # 0 FP64, 1 mixed (FP32 inner, FP64 refinement)
+    limiter: int = 0              # 0 LP, 1 Minerbo, 2 none
+    rtol: float = 1e-10           # cell-wise relative residual
+    max_iter: int = 200000
+    inner_rtol: float = 0.1
+    max_refine: int = 200
+    spin_limit: int = 0
+    restart: int = 0
+    timing: int = 0
+
+    def to_c(self) -> N.SolverOpts:
+        o = N.SolverOpts()
+        N.load().gq_solver_opts_default(ctypes.byref(o))
+        o.prec, o.limiter, o.rtol, o.max_iter = int(self.prec), int(self.limiter), float(self.rtol), int(self.max_iter)
+        o.inner_rtol, o.max_refine = float(self.inner_rtol), int(self.max_refine)
+        o.spin_limit, o.restart, o.timing = int(self.spin_limit), int(self.restart), int(self.timing)
+        return o
+
+
+class FLDPlan:
+    """gq_fld_setup / gq_fld_step / gq_fld_destroy for one grid on the current CUDA device."""
+
+    def __init__(self, x_faces, y_faces, coord: int = 0, area_x=None, area_y=None, volume=None):
+        L = N.load()
+        xf = np.ascontiguousarray(x_faces, dtype=np.float64)
+        yf = np.ascontiguousarray(y_faces, dtype=np.float64)
+        self.nx, self.ny, self.coord = xf.size - 1, yf.size - 1, int(coord)
+        g = N.GridDesc()
+        g.nx, g.ny, g.coord = self.nx, self.ny, self.coord
+        g.x_faces, _a = _host_ptr(xf)
+        g.y_faces, _b = _host_ptr(yf)
+        g.area_x, _c = _host_ptr(area_x)
+        g.area_y, _d = _host_ptr(area_y)
+        g.volume, _e = _host_ptr(volume)
+        h = ctypes.c_void_p()
+        self.device = torch.cuda.current_device()
+        rc = L.gq_fld_setup(ctypes.byref(g), ctypes.byref(h))
+        if rc != N.GQ_OK:
+            raise N.GQError(rc, "gq_fld_setup")
+        self._h = h
+
+    @classmethod
+    def for_problem(cls, p: FLDProblem) -> "FLDPlan":
+        return cls(p.x_faces, p.y_faces, p.coord)
+
+    @property
+    def nbytes(self) -> int:
+        return int(N.load().gq_fld_plan_bytes(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            N.load().gq_fld_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, t: torch.Tensor, name: str):
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a torch.Tensor")
+        if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+        if t.numel() != self.nx * self.ny:
+            raise ValueError(f"{name} has {t.numel()} elements, expected {self.nx * self.ny}")
+        if t.device.index != self.device:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, plan on cuda:{self.device}")
+
+    def step(self, rho: torch.Tensor, e_g: torch.Tensor, E_r: torch.Tensor, T_out: Optional[torch.Tensor] = None,
+             *, opacity_R: Sequence[float], opacity_P: Sequence[float], gamma: float, mu: float, dt: float,
+             bc: Sequence[int], opts: SolverOptions, stream: Optional[torch.cuda.Stream] = None,
+             check: bool = True) -> dict:
+        """One implicit step; e_g and E_r are updated in place, T_out receives T_g^{n+1}."""
+        for t, n in ((rho, "rho"), (e_g, "e_g"), (E_r, "E_r")):
+            self._check(t, n)
+        if T_out is not None:
+            self._check(T_out, "T_out")
+        op = N.OpacityLaw(*[float(v) for v in tuple(opacity_R) + tuple(opacity_P)])
+        eos = N.Eos(float(gamma), float(mu))
+        b = N.Bc()
+        for i in range(4):
+            b.side[i] = int(bc[i])
+        o = opts.to_c()
+        info = N.StepInfo()
+        st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        rc = N.load().gq_fld_step(self._h, rho.data_ptr(), e_g.data_ptr(), E_r.data_ptr(),
+                                  T_out.data_ptr() if T_out is not None else None,
+                                  ctypes.byref(op), ctypes.byref(eos), float(dt), ctypes.byref(b),
+                                  ctypes.byref(o), ctypes.c_void_p(st), ctypes.byref(info))
+        out = info.as_dict()
+        out["status"] = rc
+        if check and rc not in (N.GQ_OK,):
+            raise N.GQError(rc, "gq_fld_step")
+        return out
+
+
+def device_fields(p: FLDProblem, device="cuda"):
+    """Copy a problem's fields to the device (float64): rho, e_g, E_r, T_out."""
+    rho = torch.from_numpy(np.ascontiguousarray(p.rho)).to(device)
+    e_g = torch.from_numpy(np.ascontiguousarray(p.e_g)).to(device)
+    E_r = torch.from_numpy(np.ascontiguousarray(p.E_r)).to(device)
+    T = torch.empty_like(rho)
+    return rho, e_g, E_r, T
+
+
+def step_problem(plan: FLDPlan, p: FLDProblem, rho, e_g, E_r, T_out=None, *, prec=None, rtol=None,
+                 check=True, **kw) -> dict:
+    """One step of problem p with its own settings (limiter, bc, dt, precision, rtol)."""
+    opts = SolverOptions(prec=p.precision if prec is None else prec, limiter=p.limiter,
+                         rtol=p.rtol if rtol is None else rtol, **kw)
+    return plan.step(rho, e_g, E_r, T_out, opacity_R=p.opacity_R, opacity_P=p.opacity_P, gamma=p.gamma,
+                     mu=p.mu, dt=p.dt, bc=p.bc, opts=opts, check=check)

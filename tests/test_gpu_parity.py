@@ -1,0 +1,185 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle on the same
+seeded inputs, element by element.
+
+Gates: FP64 path <= 1e-10 and mixed path <= 1e-8 maximum per-cell relative error in
+E_r and T_g (and e_g); energy conservation 1e-12 with reflecting boundaries; error
+statuses for bad inputs, non-convergence and an inter-block wait that runs out.
+"""
+import numpy as np
+import pytest
+
+from paper_2602_12545_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FP64_GATE = 1e-10
+MIXED_GATE = 1e-8
+
+
+@pytest.fixture(scope="module")
+def fld():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2602_12545_gb300 import build
+    build.build()
+    from paper_2602_12545_gb300 import fld as F
+    return F
+
+
+def relerr(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.max(np.abs(a - b) / np.abs(b)))
+
+
+def run_gpu(F, P, prec, rtol, **kw):
+    import torch
+    plan = F.FLDPlan.for_problem(P)
+    rho, e_g, E, T = F.device_fields(P)
+    info = F.step_problem(plan, P, rho, e_g, E, T, prec=prec, rtol=rtol, **kw)
+    torch.cuda.synchronize()
+    out = {"E_r": E.cpu().numpy(), "T_g": T.cpu().numpy(), "e_g": e_g.cpu().numpy(), "info": info}
+    plan.close()
+    return out
+
+
+def check_parity(out, ref, gate):
+    for f in ("E_r", "T_g", "e_g"):
+        err = relerr(out[f], ref[f])
+        assert err <= gate, f"{f}: max rel err {err:.3e} > {gate:.0e}"
+
+
+# ----------------------------------------------------------------------------
+# config 0 (64 x 64 Cartesian), both precisions
+# ----------------------------------------------------------------------------
+
+def test_config0_fp64(fld, orc):
+    P = W.config0()
+    ref = orc.step(P, "lu")
+    out = run_gpu(fld, P, W.PREC_FP64, 1e-12)
+    assert out["info"]["status"] == 0
+    check_parity(out, ref, FP64_GATE)
+    e0, e1 = out["info"]["energy_before"], out["info"]["energy_after"]
+    assert abs(e1 - e0) <= 1e-12 * e0
+    assert e0 == pytest.approx(ref["energy_before"], rel=1e-13)
+
+
+def test_config0_mixed(fld, orc):
+    P = W.config0()
+    ref = orc.step(P, "lu")
+    out = run_gpu(fld, P, W.PREC_MIXED, 1e-10)
+    assert out["info"]["status"] == 0
+    check_parity(out, ref, MIXED_GATE)
+    assert out["info"]["refinements"] >= 1
+
+
+# ----------------------------------------------------------------------------
+# small random grids: odd sizes, both geometries, all boundary combinations,
+# all limiters; ragged against the 512-thread blocks
+# ----------------------------------------------------------------------------
+
+CASES = []
+for (nx, ny) in [(1, 1), (3, 3), (17, 9), (1, 40), (40, 1), (67, 45), (130, 33)]:
+    for coord in (W.CARTESIAN, W.SPHERICAL):
+        CASES.append((nx, ny, coord))
+
+
+@pytest.mark.parametrize("nx,ny,coord", CASES)
+@pytest.mark.parametrize("prec", [W.PREC_FP64, W.PREC_MIXED])
+def test_small_grids(fld, orc, nx, ny, coord, prec):
+    seed = 100 + nx * 7 + ny * 13 + coord
+    rng = np.random.default_rng(seed)
+    bc = tuple(int(b) for b in rng.integers(0, 2, 4))
+    limiter = int(rng.integers(0, 3))
+    P = W.random_small(nx, ny, coord, bc, seed, limiter=limiter)
+    ref = orc.step(P, "lu")
+    rtol = 1e-12 if prec == W.PREC_FP64 else 1e-11
+    out = run_gpu(fld, P, prec, rtol)
+    assert out["info"]["status"] == 0, out["info"]
+    check_parity(out, ref, FP64_GATE if prec == W.PREC_FP64 else MIXED_GATE)
+
+
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 1, 1, 1), (0, 1, 0, 0), (1, 0, 1, 0)])
+def test_boundary_combinations(fld, orc, bc):
+    P = W.random_small(23, 19, W.CARTESIAN, bc, 77)
+    ref = orc.step(P, "lu")
+    out = run_gpu(fld, P, W.PREC_FP64, 1e-12)
+    check_parity(out, ref, FP64_GATE)
+    if bc == (0, 0, 0, 0):
+        e0, e1 = out["info"]["energy_before"], out["info"]["energy_after"]
+        assert abs(e1 - e0) <= 1e-12 * e0
+    else:
+        assert out["info"]["energy_after"] < out["info"]["energy_before"]
+
+
+def test_no_coupling_and_uniform_fields(fld, orc):
+    """Degenerate cases: kappa_P = 0 (pure diffusion, T unchanged) and uniform fields."""
+    P = W.random_small(20, 14, W.CARTESIAN, (0, 0, 0, 0), 5)
+    P.opacity_P = (0.0, 0.0, 1.0, 0.0)
+    ref = orc.step(P, "lu")
+    out = run_gpu(fld, P, W.PREC_FP64, 1e-12)
+    check_parity(out, ref, FP64_GATE)
+    Q = W.random_small(12, 12, W.SPHERICAL, (0, 1, 0, 0), 6)
+    Q.rho[:] = 1e-9
+    Q.e_g[:] = Q.e_g.mean()
+    Q.E_r[:] = Q.E_r.mean()
+    ref = orc.step(Q, "lu")
+    out = run_gpu(fld, Q, W.PREC_MIXED, 1e-11)
+    check_parity(out, ref, MIXED_GATE)
+
+
+def test_deterministic(fld):
+    P = W.random_small(67, 45, W.SPHERICAL, (0, 1, 0, 0), 9)
+    a = run_gpu(fld, P, W.PREC_MIXED, 1e-10)
+    b = run_gpu(fld, P, W.PREC_MIXED, 1e-10)
+    assert np.array_equal(a["E_r"], b["E_r"]) and np.array_equal(a["T_g"], b["T_g"])
+    assert a["info"]["iterations"] == b["info"]["iterations"]
+
+
+# ----------------------------------------------------------------------------
+# error paths (host-visible statuses; nothing faults or hangs)
+# ----------------------------------------------------------------------------
+
+def test_invalid_inputs_rejected(fld):
+    import torch
+    F = fld
+    P = W.random_small(16, 16, W.CARTESIAN, (0, 0, 0, 0), 3)
+    plan = F.FLDPlan.for_problem(P)
+    for bad, code in ((-1.0, 1), (float("nan"), 5), (0.0, 1)):
+        rho, e_g, E, T = F.device_fields(P)
+        rho[3, 4] = bad
+        E0 = E.clone()
+        info = F.step_problem(plan, P, rho, e_g, E, T, check=False)
+        assert info["status"] == code
+        assert torch.equal(E, E0)          # outputs untouched on error
+    plan.close()
+
+
+def test_not_converged_status(fld):
+    F = fld
+    P = W.config0()
+    plan = F.FLDPlan.for_problem(P)
+    rho, e_g, E, T = F.device_fields(P)
+    info = F.step_problem(plan, P, rho, e_g, E, T, max_iter=2, check=False)
+    assert info["status"] == 4 and info["iterations"] == 2
+    plan.close()
+
+
+def test_barrier_spin_limit_times_out_and_recovers(fld, orc):
+    """A tiny spin limit makes the inter-block waits give up: the step returns
+    GQ_ERR_TIMEOUT (no hang, no trap) and the next step on the same context works."""
+    F = fld
+    P = W.random_small(200, 150, W.CARTESIAN, (0, 0, 0, 0), 4)   # 30000 cells: many blocks
+    plan = F.FLDPlan.for_problem(P)
+    rho, e_g, E, T = F.device_fields(P)
+    E0 = E.clone()
+    info = F.step_problem(plan, P, rho, e_g, E, T, spin_limit=1, check=False)
+    assert info["status"] == 6
+    import torch
+    assert torch.equal(E, E0)
+    info = F.step_problem(plan, P, rho, e_g, E, T, rtol=1e-12)
+    assert info["status"] == 0
+    ref = orc.step(P, "lu")
+    assert relerr(E.cpu().numpy(), ref["E_r"]) <= FP64_GATE
+    plan.close()
