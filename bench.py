@@ -41,6 +41,9 @@ FALLBACK_HBM = 6800.0
 BYTES_ITER = {1: 32.0, 0: 64.0}       # 2 coefficients + (x, r, p) read and written
 BYTES_RESID = {1: 60.0, 0: 40.0}      # FP64 residual (c_W, c_S, b, y in; r out) [+ y += d for mixed]
 KERNELS_PER_STEP = 7                  # cells, faces, diag, scale, pcg, backsub, finalize
+# cell-wise residual target of the spherical workload: the loosest setting whose E and T
+# agree with the tightly solved FP64 answer to 1e-8 per cell (reported in the line)
+DEFAULT_C2_RTOL = 1e-11
 
 
 def parse():
@@ -201,7 +204,7 @@ def run_ours(args):
             dist.barrier()
 
     P, desc = workload(args.workload)
-    rtol = args.rtol if args.rtol is not None else (1e-8 if args.workload == "c2" else P.rtol)
+    rtol = args.rtol if args.rtol is not None else (DEFAULT_C2_RTOL if args.workload == "c2" else P.rtol)
     prec = 1 if args.workload == "c2" else P.precision
     plan = F.FLDPlan.for_problem(P)
     rho0, eg0, E0, _ = F.device_fields(P)
@@ -210,7 +213,7 @@ def run_ours(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def one(opts):
+    def one(opts, check=True):
         e_g.copy_(eg0)
         E.copy_(E0)
         flush.fill_(1.0)
@@ -218,7 +221,7 @@ def run_ours(args):
         s1 = torch.cuda.Event(enable_timing=True)
         s0.record(stream)
         info = plan.step(rho, e_g, E, T, opacity_R=P.opacity_R, opacity_P=P.opacity_P, gamma=P.gamma, mu=P.mu,
-                         dt=P.dt, bc=P.bc, opts=opts)
+                         dt=P.dt, bc=P.bc, opts=opts, check=check)
         s1.record(stream)
         s1.synchronize()
         info["ms"] = s0.elapsed_time(s1)
@@ -227,7 +230,9 @@ def run_ours(args):
     opts = F.SolverOptions(prec=prec, limiter=P.limiter, rtol=rtol, timing=1)
     # accuracy reference: FP64 path solved tightly (untimed)
     ref_opts = F.SolverOptions(prec=0, limiter=P.limiter, rtol=1e-13, timing=0, max_iter=1000000)
-    one(ref_opts)
+    ref_info = one(ref_opts, check=False)       # may stop at the FP64 floor (status 4)
+    if ref_info["status"] not in (0, 4):
+        raise RuntimeError(f"reference solve failed: {ref_info}")
     E_ref, T_ref = E.clone(), T.clone()
 
     for _ in range(args.warmup):
@@ -354,8 +359,8 @@ def run_reference(args):
     if rank != 0:
         return
     P, desc = workload(args.workload)
-    rtol = args.rtol if args.rtol is not None else (1e-8 if args.workload == "c2" else P.rtol)
-    iters = {"c0": 148, "c1": 1264, "c2": 4500}[args.workload]
+    rtol = args.rtol if args.rtol is not None else (DEFAULT_C2_RTOL if args.workload == "c2" else P.rtol)
+    iters = {"c0": 174, "c1": 1454, "c2": 4500}[args.workload]
     for _ in range(args.warmup):
         oracle_sample(P, iters, cg_iters=10)
     samples = []

@@ -151,6 +151,84 @@ gq_status gq_fld_step(gq_fld_plan *plan, const double *rho, double *e_g, double 
 /* Release a plan and its device memory (NULL is ignored). */
 void gq_fld_destroy(gq_fld_plan *plan);
 
+/* ---------------------------------------------------------------------------------------
+ * Batched steps: many independent problems (each with its own plan, i.e. its own grid,
+ * Cartesian or spherical-polar, and its own dt, opacity law, boundaries and options) in
+ * one persistent cooperative launch.  Each problem is exactly the step of gq_fld_step;
+ * batching changes only how the GPU is shared: a problem is solved by a team of blocks
+ * sized to it, teams pull problems from per-size queues (largest work first), and the
+ * whole step (set-up, solve, back-substitution, result gather) is captured once in a
+ * CUDA graph and replayed.  Not in the paper: its code solves one grid per MPI job.
+ * --------------------------------------------------------------------------------------- */
+
+/* One problem of a batched step: the arguments of gq_fld_step, by value. */
+typedef struct {
+    const double *rho;
+    double *e_g;
+    double *E_r;
+    double *T_g_out;              /* may be NULL */
+    gq_opacity_law opacity;
+    gq_eos eos;
+    double dt;
+    gq_bc bc;
+    gq_solver_opts opts;
+} gq_batch_item;
+
+/* Batch schedule options.
+ *   cells_per_block  a problem's team has about N / cells_per_block blocks (power of two)
+ *   max_team         largest team, in blocks
+ *   use_graph        1: capture the batched step in a CUDA graph on first use and replay it
+ * Zero fields take the value the autotuner cached for the batch's shape class, else
+ * 32768 cells per block and teams of at most 16 blocks. */
+typedef struct {
+    int cells_per_block;
+    int max_team;
+    int use_graph;
+    int reserved[5];
+} gq_batch_opts;
+
+typedef struct gq_batch gq_batch;
+
+/* Defaults: cells_per_block 0, max_team 0 (autotuned or built-in), use_graph 1. */
+void gq_batch_opts_default(gq_batch_opts *opts);
+
+/* Create a batch over n >= 1 plans on one device (host array of plan pointers, copied;
+ * the plans must outlive the batch).  Allocates the schedule tables, a private stream
+ * and pinned staging.  Errors: GQ_ERR_INVALID_ARG, GQ_ERR_OOM, GQ_ERR_CUDA. */
+gq_status gq_batch_create(gq_fld_plan *const *plans, int n, const gq_batch_opts *opts, gq_batch **out);
+
+/* One step of every problem: items is a host array of n items (device field pointers
+ * as in gq_fld_step), infos a host array of n results (may be NULL).  The step is
+ * ordered after prior work on `stream` and later work on `stream` waits for it; the
+ * call returns when it has completed.  Returns GQ_OK, or the first non-OK per-problem
+ * status (each problem's own status is in infos[p].status); GQ_ERR_INVALID_ARG for a
+ * bad item before anything runs.  infos[p].t_solve_ms is the whole batch's device time. */
+gq_status gq_batch_step(gq_batch *batch, const gq_batch_item *items, void *stream, gq_step_info *infos);
+
+/* Rebuild the schedule with new options (NULL keeps them) from the latest per-problem
+ * iteration counts; drops the captured graph. */
+gq_status gq_batch_reschedule(gq_batch *batch, const gq_batch_opts *opts);
+
+/* Autotune cells_per_block x max_team by timing full batched steps on the given items
+ * (their e_g and E_r are restored afterwards; a temporary device copy of them is
+ * allocated).  Keeps the fastest schedule, caches it for the batch's shape class, and
+ * reports it (best and best_ms may be NULL). */
+gq_status gq_batch_autotune(gq_batch *batch, const gq_batch_item *items, void *stream, gq_batch_opts *best,
+                            double *best_ms);
+
+/* Device time of the last gq_batch_step, in ms. */
+double gq_batch_last_step_ms(const gq_batch *batch);
+
+/* 1 if the batch replays a captured CUDA graph, 0 if it launches eagerly. */
+int gq_batch_uses_graph(const gq_batch *batch);
+
+/* Release a batch (not its plans; NULL is ignored). */
+void gq_batch_destroy(gq_batch *batch);
+
+/* One batched step without keeping a batch (no graph): create, step, destroy. */
+gq_status gq_fld_step_batched(gq_fld_plan *const *plans, int n, const gq_batch_item *items, void *stream,
+                              gq_step_info *infos);
+
 /* Default solver options: FP64, LP limiter, rtol 1e-10, max_iter 200000, inner_rtol 0.1,
  * max_refine 200, default spin limit, keep the search direction. */
 void gq_solver_opts_default(gq_solver_opts *opts);

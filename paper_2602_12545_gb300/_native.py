@@ -59,6 +59,17 @@ class StepInfo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("rho", ctypes.c_void_p), ("e_g", ctypes.c_void_p), ("E_r", ctypes.c_void_p),
+                ("T_g_out", ctypes.c_void_p), ("opacity", OpacityLaw), ("eos", Eos), ("dt", ctypes.c_double),
+                ("bc", Bc), ("opts", SolverOpts)]
+
+
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("cells_per_block", ctypes.c_int), ("max_team", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
+
+
 # every symbol include/gq_fld.h declares, with (restype, argtypes)
 SIGNATURES = {
     "gq_fld_setup": (ctypes.c_int, [ctypes.POINTER(GridDesc), ctypes.POINTER(ctypes.c_void_p)]),
@@ -71,6 +82,19 @@ SIGNATURES = {
     "gq_solver_opts_default": (None, [ctypes.POINTER(SolverOpts)]),
     "gq_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "gq_version": (ctypes.c_char_p, []),
+    "gq_batch_opts_default": (None, [ctypes.POINTER(BatchOpts)]),
+    "gq_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(BatchOpts),
+                                       ctypes.POINTER(ctypes.c_void_p)]),
+    "gq_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(BatchItem), ctypes.c_void_p,
+                                     ctypes.POINTER(StepInfo)]),
+    "gq_batch_reschedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(BatchOpts)]),
+    "gq_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(BatchItem), ctypes.c_void_p,
+                                         ctypes.POINTER(BatchOpts), ctypes.POINTER(ctypes.c_double)]),
+    "gq_batch_last_step_ms": (ctypes.c_double, [ctypes.c_void_p]),
+    "gq_batch_uses_graph": (ctypes.c_int, [ctypes.c_void_p]),
+    "gq_batch_destroy": (None, [ctypes.c_void_p]),
+    "gq_fld_step_batched": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(BatchItem),
+                                           ctypes.c_void_p, ctypes.POINTER(StepInfo)]),
 }
 
 _lock = threading.Lock()

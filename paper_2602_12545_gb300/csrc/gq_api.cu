@@ -9,23 +9,8 @@
 #include "gq_device.cuh"
 #include "gq_internal.h"
 
-struct gq_fld_plan {
-    int nx, ny, N, coord;
-    int device;
-    int num_sms;
-    int solve_grid_max;     // co-resident blocks of the solve kernel
-    int setup_blocks;
-    void* arena;
-    size_t arena_bytes;
-    gq::DeviceGeometry geo;
-    gq::Workspace ws;
-    gq::SolveCtl* ctl_host;  // pinned
-    cudaEvent_t ev[4];       // phase timing
-};
-
 namespace {
 
-constexpr int64_t kDefaultSpin = 1ll << 24;
 
 // ---------------------------------------------------------------------------
 // host geometry (FP64): volumes, face areas, volume centres, centre distances
@@ -195,6 +180,85 @@ bool finite_all(const double* v, int n) {
 
 }  // namespace
 
+namespace gq {
+
+gq_status make_step_params(const gq_fld_plan* P, const double* rho, double* e_g, double* E_r, double* T_g_out,
+                           const gq_opacity_law* op, const gq_eos* eos, double dt, const gq_bc* bc,
+                           const gq_solver_opts* opts_in, StepParams* sp_out, SolveParams* pp_out,
+                           int* timing) {
+    if (!P || !rho || !e_g || !E_r || !op || !eos || !bc) return GQ_ERR_INVALID_ARG;
+    gq_solver_opts opts;
+    if (opts_in) opts = *opts_in;
+    else gq_solver_opts_default(&opts);
+    const double kR[4] = {op->k0_R, op->k1_R, op->a_R, op->b_R};
+    const double kP[4] = {op->k0_P, op->k1_P, op->a_P, op->b_P};
+    if (!finite_all(kR, 4) || !finite_all(kP, 4)) return GQ_ERR_INVALID_ARG;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return GQ_ERR_INVALID_ARG;
+    if (!(eos->gamma > 1.0) || !(eos->mu > 0.0) || !std::isfinite(eos->gamma) || !std::isfinite(eos->mu))
+        return GQ_ERR_INVALID_ARG;
+    for (int s = 0; s < 4; s++)
+        if (bc->side[s] != GQ_BC_REFLECT && bc->side[s] != GQ_BC_OUTFLOW_MILNE) return GQ_ERR_INVALID_ARG;
+    if (opts.prec != GQ_PREC_FP64 && opts.prec != GQ_PREC_MIXED) return GQ_ERR_INVALID_ARG;
+    if (opts.limiter < GQ_LIMITER_LP || opts.limiter > GQ_LIMITER_NONE) return GQ_ERR_INVALID_ARG;
+    if (!(opts.rtol > 0.0) || !(opts.rtol < 1.0) || opts.max_iter < 1) return GQ_ERR_INVALID_ARG;
+    if (opts.prec == GQ_PREC_MIXED && (!(opts.inner_rtol > 0.0) || !(opts.inner_rtol < 1.0)))
+        return GQ_ERR_INVALID_ARG;
+    if (opts.max_refine < 1 || opts.spin_limit < 0) return GQ_ERR_INVALID_ARG;
+
+    StepParams sp{};
+    sp.nx = P->nx;
+    sp.ny = P->ny;
+    sp.N = P->N;
+    for (int s = 0; s < 4; s++) sp.bc[s] = bc->side[s];
+    sp.limiter = opts.limiter;
+    sp.mixed = opts.prec == GQ_PREC_MIXED;
+    for (int t = 0; t < 4; t++) {
+        sp.kR[t] = kR[t];
+        sp.kP[t] = kP[t];
+    }
+    sp.cvfac = kKB / ((eos->gamma - 1.0) * eos->mu * kMH);
+    sp.dt = dt;
+    sp.rho = rho;
+    sp.eg = e_g;
+    sp.E = E_r;
+    sp.eg_out = e_g;
+    sp.T_out = T_g_out;
+
+    SolveParams pp{};
+    pp.nx = P->nx;
+    pp.N = P->N;
+    pp.mixed = sp.mixed;
+    pp.restart = opts.restart;
+    pp.max_iter = opts.max_iter;
+    pp.max_refine = opts.max_refine;
+    pp.rtol = opts.rtol;
+    pp.drop = opts.inner_rtol;
+    pp.spin_limit = opts.spin_limit > 0 ? opts.spin_limit : kDefaultSpin;
+    *sp_out = sp;
+    *pp_out = pp;
+    if (timing) *timing = opts.timing;
+    return GQ_OK;
+}
+
+gq_status status_of(const SolveCtl& c) {
+    if (c.input_flags & 2) return GQ_ERR_NONFINITE;
+    if (c.input_flags & 1) return GQ_ERR_INVALID_ARG;
+    if (c.abort || c.status == kPending) return GQ_ERR_TIMEOUT;
+    return static_cast<gq_status>(c.status);
+}
+
+void fill_info(const SolveCtl& c, gq_status status, gq_step_info* info) {
+    info->iterations = c.iterations;
+    info->refinements = c.refinements;
+    info->rel_residual = c.crit;
+    info->rel_residual_l2 = c.l2;
+    info->energy_before = c.energy0;
+    info->energy_after = c.energy1;
+    info->status = status;
+}
+
+}  // namespace gq
+
 extern "C" {
 
 const char* gq_version(void) { return "0.1.0"; }
@@ -315,62 +379,18 @@ gq_status gq_fld_step(gq_fld_plan* P, const double* rho, double* e_g, double* E_
         std::memset(info, 0, sizeof(*info));
         info->status = GQ_ERR_INVALID_ARG;
     }
-    if (!P || !rho || !e_g || !E_r || !op || !eos || !bc) return GQ_ERR_INVALID_ARG;
-    gq_solver_opts opts;
-    if (opts_in) opts = *opts_in;
-    else gq_solver_opts_default(&opts);
-    const double kR[4] = {op->k0_R, op->k1_R, op->a_R, op->b_R};
-    const double kP[4] = {op->k0_P, op->k1_P, op->a_P, op->b_P};
-    if (!finite_all(kR, 4) || !finite_all(kP, 4)) return GQ_ERR_INVALID_ARG;
-    if (!(dt > 0.0) || !std::isfinite(dt)) return GQ_ERR_INVALID_ARG;
-    if (!(eos->gamma > 1.0) || !(eos->mu > 0.0) || !std::isfinite(eos->gamma) || !std::isfinite(eos->mu))
-        return GQ_ERR_INVALID_ARG;
-    for (int s = 0; s < 4; s++)
-        if (bc->side[s] != GQ_BC_REFLECT && bc->side[s] != GQ_BC_OUTFLOW_MILNE) return GQ_ERR_INVALID_ARG;
-    if (opts.prec != GQ_PREC_FP64 && opts.prec != GQ_PREC_MIXED) return GQ_ERR_INVALID_ARG;
-    if (opts.limiter < GQ_LIMITER_LP || opts.limiter > GQ_LIMITER_NONE) return GQ_ERR_INVALID_ARG;
-    if (!(opts.rtol > 0.0) || !(opts.rtol < 1.0) || opts.max_iter < 1) return GQ_ERR_INVALID_ARG;
-    if (opts.prec == GQ_PREC_MIXED &&
-        (!(opts.inner_rtol > 0.0) || !(opts.inner_rtol < 1.0) || opts.max_refine < 1))
-        return GQ_ERR_INVALID_ARG;
-    if (opts.spin_limit < 0) return GQ_ERR_INVALID_ARG;
+    gq::StepParams sp{};
+    gq::SolveParams pp{};
+    int timing_flag = 0;
+    gq_status vs = gq::make_step_params(P, rho, e_g, E_r, T_g_out, op, eos, dt, bc, opts_in, &sp, &pp, &timing_flag);
+    if (vs != GQ_OK) return vs;
 
     int cur = -1;
     if (cudaGetDevice(&cur) != cudaSuccess) return GQ_ERR_CUDA;
     if (cur != P->device && cudaSetDevice(P->device) != cudaSuccess) return GQ_ERR_CUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 
-    gq::StepParams sp{};
-    sp.nx = P->nx;
-    sp.ny = P->ny;
-    sp.N = P->N;
-    for (int s = 0; s < 4; s++) sp.bc[s] = bc->side[s];
-    sp.limiter = opts.limiter;
-    sp.mixed = opts.prec == GQ_PREC_MIXED;
-    for (int t = 0; t < 4; t++) {
-        sp.kR[t] = kR[t];
-        sp.kP[t] = kP[t];
-    }
-    sp.cvfac = gq::kKB / ((eos->gamma - 1.0) * eos->mu * gq::kMH);
-    sp.dt = dt;
-    sp.rho = rho;
-    sp.eg = e_g;
-    sp.E = E_r;
-    sp.eg_out = e_g;
-    sp.T_out = T_g_out;
-
-    gq::SolveParams pp{};
-    pp.nx = P->nx;
-    pp.N = P->N;
-    pp.mixed = sp.mixed;
-    pp.restart = opts.restart;
-    pp.max_iter = opts.max_iter;
-    pp.max_refine = opts.max_refine;
-    pp.rtol = opts.rtol;
-    pp.drop = opts.inner_rtol;
-    pp.spin_limit = opts.spin_limit > 0 ? opts.spin_limit : kDefaultSpin;
-
-    const bool timing = opts.timing != 0;
+    const bool timing = timing_flag != 0;
     cudaError_t e = cudaMemsetAsync(P->ws.ctl, 0, sizeof(gq::SolveCtl), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->ws.bar, 0, 2 * sizeof(unsigned), st);
     if (e == cudaSuccess && timing) e = cudaEventRecord(P->ev[0], st);
@@ -389,19 +409,9 @@ gq_status gq_fld_step(gq_fld_plan* P, const double* rho, double* e_g, double* E_
         return GQ_ERR_CUDA;
     }
     const gq::SolveCtl& c = *P->ctl_host;
-    gq_status status;
-    if (c.input_flags & 2) status = GQ_ERR_NONFINITE;
-    else if (c.input_flags & 1) status = GQ_ERR_INVALID_ARG;
-    else if (c.abort) status = GQ_ERR_TIMEOUT;
-    else status = static_cast<gq_status>(c.status);
+    const gq_status status = gq::status_of(c);
     if (info) {
-        info->iterations = c.iterations;
-        info->refinements = c.refinements;
-        info->rel_residual = c.crit;
-        info->rel_residual_l2 = c.l2;
-        info->energy_before = c.energy0;
-        info->energy_after = c.energy1;
-        info->status = status;
+        gq::fill_info(c, status, info);
         info->solve_blocks = P->solve_grid_max;
         if (timing) {
             float t0 = 0.f, t1 = 0.f, t2 = 0.f;

@@ -55,50 +55,53 @@ __device__ __forceinline__ double warp_reduce(double v) {
 }
 
 // ---------------------------------------------------------------------------
-// bounded inter-block barrier for co-resident (cooperatively launched) grids.
-// bar[0] counts arrivals, bar[1] is the generation.  A block that polls longer than
-// spin_limit iterations (or sees *abort set) gives up, sets *abort and returns false;
-// every caller must then leave the kernel.  No wait in this library is unbounded.
+// Bounded barrier of a team of co-resident blocks (rank in [0, size)).  One 32-bit
+// word per team: every block adds 1, except rank 0 which adds 2^31 - (size - 1), so
+// the word's top bit flips exactly when the last block arrives and its low bits return
+// to where they were (no reset between barriers).  The arrival is an acquire-release
+// atomic and the poll an acquire load, so writes before the barrier are visible after
+// it.  A block that polls more than spin_limit times (or sees *abort_flag set) gives up,
+// sets *abort_flag and returns false; every caller must then leave the kernel.  No wait
+// in this library is unbounded.
 // ---------------------------------------------------------------------------
+struct Team {
+    int rank;
+    int size;
+};
+
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
 
-__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
 }
 
 __device__ __forceinline__ int ld_volatile_int(const int* p) {
     return *reinterpret_cast<const volatile int*>(p);
 }
 
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, long long spin_limit,
-                                             int* abort_flag) {
+__device__ __forceinline__ bool team_barrier(unsigned* bar, Team team, long long spin_limit, int* abort_flag) {
     __shared__ int s_ok;
     __syncthreads();
+    if (team.size == 1) return true;     // a one-block team needs only the block barrier
     if (threadIdx.x == 0) {
         int ok = 1;
-        unsigned gen = ld_acquire_gpu(bar + 1);
-        __threadfence();
-        unsigned prev = atomicAdd(bar, 1u);
-        if (prev == nblocks - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            st_release_gpu(bar + 1, gen + 1u);
-        } else {
-            long long n = 0;
-            while (ld_acquire_gpu(bar + 1) == gen) {
-                if (++n > spin_limit || ld_volatile_int(abort_flag)) {
-                    atomicExch(abort_flag, 1);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(32);
+        const unsigned inc = team.rank == 0 ? 0x80000000u - (unsigned)(team.size - 1) : 1u;
+        const unsigned old = atom_add_acq_rel_gpu(bar, inc);
+        long long n = 0;
+        while (((ld_acquire_gpu(bar) ^ old) & 0x80000000u) == 0u) {
+            if (++n > spin_limit || ld_volatile_int(abort_flag)) {
+                atomicExch(abort_flag, 1);
+                ok = 0;
+                break;
             }
+            __nanosleep(20);
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();

@@ -82,6 +82,43 @@ struct SolveParams {
     long long spin_limit;
 };
 
+// status of a problem of a batch that no team has solved yet
+constexpr int kPending = 100;
+
+// One problem of a batched step: its per-step parameters, geometry, workspace and
+// solver settings (device-resident table, one entry per problem).
+struct ProbDesc {
+    StepParams sp;
+    DeviceGeometry g;
+    Workspace w;
+    SolveParams solve;
+    int setup_blocks;    // blocks of the batched set-up launches for this problem
+    int pad;
+};
+
+// Arguments of the batched kernels.  Set-up kernels map block b to problem p with
+// setup_prefix[p] <= b < setup_prefix[p+1].  The solve kernel partitions its blocks
+// into teams; team t (team_first[t] .. + team_size[t]) takes problems of its class
+// from the class queue (largest estimated work first) until the queue is empty.
+struct BatchArgs {
+    const ProbDesc* desc;
+    int n;
+    int nclass;
+    const int* setup_prefix;   // [n+1]
+    const int* block_team;     // [G]
+    const int* team_first;     // [T]
+    const int* team_size;      // [T]
+    const int* team_class;     // [T]
+    const int* queue;          // [n]
+    const int* class_start;    // [nclass+1]
+    int* queue_head;           // [nclass]
+    int* team_slot;            // [T]
+    unsigned* team_bar;        // [2T]
+    int* abort_flag;
+    long long spin_limit;
+    SolveCtl* ctl_out;         // [n] gathered control blocks
+};
+
 // launchers (stream-ordered)
 cudaError_t launch_setup(const StepParams& sp, const DeviceGeometry& g, const Workspace& w,
                          int setup_blocks, cudaStream_t st);
@@ -89,5 +126,35 @@ cudaError_t launch_solve(const SolveParams& p, const Workspace& w, int grid, cud
 cudaError_t launch_backsub(const StepParams& sp, const DeviceGeometry& g, const Workspace& w,
                            int setup_blocks, cudaStream_t st);
 int solve_max_blocks_per_sm();
+int batch_solve_max_blocks_per_sm();
+cudaError_t launch_batch_setup(const BatchArgs& a, int total_setup_blocks, cudaStream_t st);
+cudaError_t launch_batch_solve(const BatchArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_batch_finish(const BatchArgs& a, int total_setup_blocks, cudaStream_t st);
+
+constexpr long long kDefaultSpin = 1ll << 24;
+
+// argument validation and parameter blocks shared by the single and batched steps
+gq_status make_step_params(const gq_fld_plan* P, const double* rho, double* e_g, double* E_r, double* T_g_out,
+                           const gq_opacity_law* op, const gq_eos* eos, double dt, const gq_bc* bc,
+                           const gq_solver_opts* opts, StepParams* sp, SolveParams* pp, int* timing);
+gq_status status_of(const SolveCtl& c);
+gq_status batch_create_capacity(int device, int num_sms, int cap, const gq_batch_opts* opts, gq_batch** out);
+gq_status batch_rebind(gq_batch* B, gq_fld_plan* const* plans, int n);
+void fill_info(const SolveCtl& c, gq_status status, gq_step_info* info);
 
 }  // namespace gq
+
+// A plan: one grid's geometry and the device workspace of its step.
+struct gq_fld_plan {
+    int nx, ny, N, coord;
+    int device;
+    int num_sms;
+    int solve_grid_max;      // co-resident blocks of the solve kernel (also the partials capacity)
+    int setup_blocks;
+    void* arena;
+    size_t arena_bytes;
+    gq::DeviceGeometry geo;
+    gq::Workspace ws;
+    gq::SolveCtl* ctl_host;  // pinned
+    cudaEvent_t ev[4];       // phase timing
+};

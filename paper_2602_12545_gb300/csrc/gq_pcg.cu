@@ -1,5 +1,6 @@
 // Persistent Jacobi-preconditioned conjugate-gradient solve of the reduced FLD system
-// (the Krylov step of Sec. 3.2.1, stopping rule in the spirit of Eq. linearsystem).
+// (the Krylov step of Sec. 3.2.1, with a residual-based stop in the spirit of
+// Eq. linearsystem).
 //
 // The system is solved in Jacobi-scaled form A^ y = b^ with A^ = S A S (unit diagonal,
 // off-diagonals -c_f = -w_f s_k s_m), so Jacobi-PCG on A is plain CG on A^ and the
@@ -7,24 +8,26 @@
 // west neighbour) and c_S (face to the south neighbour); the east and north
 // coefficients of cell k are c_W[k+1] and c_S[k+nx] (zero across the boundary).
 //
-// One cooperative launch runs the whole solve.  Each iteration is two grid-stride
-// passes separated by grid-wide reductions:
+// One cooperative launch runs the whole solve.  Each iteration is two passes separated
+// by team-wide reductions:
 //   S: p = r + beta p_old (p double-buffered), q = A^ p, partial p.q
 //   U: x += alpha p, r -= alpha q, partial r.r (FP64 path: also max |r_k / y_k|)
-// All blocks reduce the per-block partials in the same order, so every block takes
-// bitwise-identical control decisions without a broadcast.
+// A thread handles W consecutive cells of one row with 16-byte loads (W = 4 in FP32,
+// 2 in FP64) when nx is a multiple of W, one cell otherwise.  All blocks reduce the
+// per-block partials in the same order, so every block takes bitwise-identical control
+// decisions without a broadcast, and results are reproducible run to run.
 //
 // FP64 path: x is the FP64 iterate y.  When the recursive cell-wise residual
 // max |r_k / y_k| reaches its target (rtol, halved after every disagreeing check), the
-// true residual b^ - A^ y is recomputed (in place of r) and the stop test is applied to it.
-// Both paths end with GQ_ERR_NOT_CONVERGED (best iterate kept) when the true residual
-// has not improved by 10% in 6 consecutive checks: the FP64 rounding floor of the
-// cell-wise criterion lies above rtol.
+// true residual b^ - A^ y is recomputed (in place of r) and the stop test applied to it.
 // Mixed path: the Krylov vectors, the coefficients and the correction d are FP32.  When
 // |r|_2 has fallen by inner_rtol since the last FP64 residual, y += d (FP64), d = 0, the
 // FP64 residual is recomputed and, unless converged, becomes the new FP32 residual; the
 // search direction is kept (reliable update) unless `restart` is set.  The FP32 residual
 // is carried with a fixed power-of-two scale so that its entries stay O(1).
+// Both paths end with GQ_ERR_NOT_CONVERGED (best iterate kept) when the true residual
+// has not improved by 10% in 6 consecutive checks: the FP64 rounding floor of the
+// cell-wise criterion lies above rtol.
 #include <type_traits>
 
 #include "gq_device.cuh"
@@ -42,14 +45,69 @@ struct RedShared {
     double tot[kSlots];
 };
 
+// ---- 16-byte vector access ------------------------------------------------------------
+
+template <class R, int W>
+__device__ __forceinline__ void ldv(const R* p, R (&o)[W]) {
+    if constexpr (W == 1) {
+        o[0] = __ldcg(p);
+    } else if constexpr (std::is_same_v<R, float> && W == 4) {
+        const float4 v = __ldcg(reinterpret_cast<const float4*>(p));
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    } else {
+        static_assert(std::is_same_v<R, double> && W == 2, "unsupported vector");
+        const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+        o[0] = v.x; o[1] = v.y;
+    }
+}
+
+template <class R, int W>
+__device__ __forceinline__ void stv(R* p, const R (&o)[W]) {
+    if constexpr (W == 1) {
+        p[0] = o[0];
+    } else if constexpr (std::is_same_v<R, float> && W == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    } else {
+        *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
+    }
+}
+
+// W doubles (W = 1, 2 or 4) from an address aligned to 16 bytes when W > 1
+template <int W>
+__device__ __forceinline__ void ld64(const double* p, double (&o)[W]) {
+    if constexpr (W == 1) {
+        o[0] = __ldcg(p);
+    } else {
+#pragma unroll
+        for (int h = 0; h < W / 2; h++) {
+            const double2 v = __ldcg(reinterpret_cast<const double2*>(p) + h);
+            o[2 * h] = v.x;
+            o[2 * h + 1] = v.y;
+        }
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void st64(double* p, const double (&o)[W]) {
+    if constexpr (W == 1) {
+        p[0] = o[0];
+    } else {
+#pragma unroll
+        for (int h = 0; h < W / 2; h++)
+            reinterpret_cast<double2*>(p)[h] = make_double2(o[2 * h], o[2 * h + 1]);
+    }
+}
+
 // Block-reduce NSUM sums and NMAX maxima, publish the block partials, wait for all
-// blocks, reduce the partials (same order in every block).  Returns false on timeout.
+// blocks of the team, reduce the partials (same order in every block).  Returns false
+// on timeout.
 template <int NSUM, int NMAX>
 __device__ __forceinline__ bool allreduce(double (&v)[NSUM + NMAX], double* partials, int& parity,
-                                          unsigned* bar, long long spin, int* abort_flag, RedShared& sh) {
+                                          unsigned* bar, long long spin, int* abort_flag, RedShared& sh,
+                                          Team team) {
     constexpr int NS = NSUM + NMAX;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int G = gridDim.x;
+    const int G = team.size;
 #pragma unroll
     for (int s = 0; s < NS; s++) {
         v[s] = s < NSUM ? warp_reduce<false>(v[s]) : warp_reduce<true>(v[s]);
@@ -62,17 +120,28 @@ __device__ __forceinline__ bool allreduce(double (&v)[NSUM + NMAX], double* part
         for (int s = 0; s < NS; s++) {
             double a = lane < nw ? sh.warp[lane][s] : 0.0;
             a = s < NSUM ? warp_reduce<false>(a) : warp_reduce<true>(a);
-            if (lane == 0) mine[blockIdx.x * kSlots + s] = a;
+            if (lane == 0) mine[team.rank * kSlots + s] = a;
         }
     }
-    if (!grid_barrier(bar, G, spin, abort_flag)) return false;
+    if (!team_barrier(bar, team, spin, abort_flag)) return false;
     if (warp == 0) {
+        // all loads first: one L2 round trip for teams of up to 256 blocks
+        double x[NS][8];
+#pragma unroll
+        for (int s = 0; s < NS; s++)
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                const int b = lane + 32 * i;
+                x[s][i] = b < G ? __ldcg(mine + b * kSlots + s) : 0.0;
+            }
 #pragma unroll
         for (int s = 0; s < NS; s++) {
-            double a = 0.0;
-            for (int b = lane; b < G; b += 32) {
-                const double x = __ldcg(mine + b * kSlots + s);
-                a = s < NSUM ? a + x : nanmax(a, x);
+            double a = x[s][0];
+#pragma unroll
+            for (int i = 1; i < 8; i++) a = s < NSUM ? a + x[s][i] : nanmax(a, x[s][i]);
+            for (int b = lane + 256; b < G; b += 32) {
+                const double z = __ldcg(mine + b * kSlots + s);
+                a = s < NSUM ? a + z : nanmax(a, z);
             }
             a = s < NSUM ? warp_reduce<false>(a) : warp_reduce<true>(a);
             if (lane == 0) sh.tot[s] = a;
@@ -85,13 +154,15 @@ __device__ __forceinline__ bool allreduce(double (&v)[NSUM + NMAX], double* part
     return true;
 }
 
-template <bool MIXED>
-__global__ void __launch_bounds__(kSolveThreads, 2) k_pcg(SolveParams P, Workspace w) {
+// Solve of one problem by one team of co-resident blocks, W cells per thread and pass.
+// Returns false when a wait of the team timed out (the caller must leave the kernel).
+template <bool MIXED, int W>
+__device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspace& w, Team team, RedShared& sh) {
     using R = std::conditional_t<MIXED, float, double>;
-    __shared__ RedShared sh;
     const int N = P.N, nx = P.nx;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int stride = gridDim.x * blockDim.x;
+    const int nchunk = N / W;          // N is a multiple of W because nx is
+    const int tid = team.rank * blockDim.x + threadIdx.x;
+    const int stride = team.size * blockDim.x;
     SolveCtl* ctl = w.ctl;
     int* abort_flag = &ctl->abort;
     int parity = 0;
@@ -117,7 +188,7 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_pcg(SolveParams P, Workspa
     const int flags = __ldcg(&ctl->input_flags);
     if (flags) {
         if (tid == 0) ctl->status = (flags & 2) ? kErrNonfinite : kErrInvalid;
-        return;
+        return true;
     }
 
     // ---- FP64 residual r64 = b^ - A^ y and its norms ----------------------------------
@@ -126,28 +197,49 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_pcg(SolveParams P, Workspa
     auto true_residual = [&](bool first) -> bool {
 #pragma unroll
         for (int t = 0; t < 5; t++) tr[t] = 0.0;
-        for (int k = tid; k < N; k += stride) {
-            const double yk = __ldcg(y + k);
-            double ax = yk;
-            if (k > 0) ax -= cW64[k] * __ldcg(y + k - 1);
-            if (k + 1 < N) ax -= cW64[k + 1] * __ldcg(y + k + 1);
-            if (k >= nx) ax -= cS64[k] * __ldcg(y + k - nx);
-            if (k + nx < N) ax -= cS64[k + nx] * __ldcg(y + k + nx);
-            const double bk = bh[k];
-            const double rk = bk - ax;
-            r64[k] = rk;
-            const double sk = s[k];
-            const double ru = rk / sk;
-            tr[0] += rk * rk;
-            tr[1] += ru * ru;
-            if (first) {
-                const double bu = bk / sk;
-                tr[2] += bu * bu;
+        for (int c = tid; c < nchunk; c += stride) {
+            const int k = c * W;
+            const bool hs = k >= nx, hn = k + nx < N, hw = k > 0, he = k + W < N;
+            double yc[W], ys[W], yn[W], cw[W], cs[W], csn[W], bk[W], sk[W];
+            double yw = 0.0, ye = 0.0, cwe = 0.0;
+            ld64<W>(y + k, yc);
+            ld64<W>(cW64 + k, cw);
+            ld64<W>(cS64 + k, cs);
+            ld64<W>(bh + k, bk);
+            ld64<W>(s + k, sk);
+            if (hw) yw = __ldcg(y + k - 1);
+            if (he) {
+                ye = __ldcg(y + k + W);
+                cwe = cW64[k + W];
             }
-            tr[3] = nanmax(tr[3], fabs(rk / yk));
-            tr[4] = nanmax(tr[4], fabs(rk));
+            if (hs) ld64<W>(y + k - nx, ys);
+            if (hn) {
+                ld64<W>(y + k + nx, yn);
+                ld64<W>(cS64 + k + nx, csn);
+            }
+            double rk[W];
+#pragma unroll
+            for (int i = 0; i < W; i++) {
+                const double left = i == 0 ? yw : yc[i - 1];
+                const double right = i == W - 1 ? ye : yc[i + 1];
+                const double cright = i == W - 1 ? cwe : cw[i + 1];
+                double ax = yc[i] - cw[i] * left - cright * right;
+                if (hs) ax -= cs[i] * ys[i];
+                if (hn) ax -= csn[i] * yn[i];
+                rk[i] = bk[i] - ax;
+                const double ru = rk[i] / sk[i];
+                tr[0] += rk[i] * rk[i];
+                tr[1] += ru * ru;
+                if (first) {
+                    const double bu = bk[i] / sk[i];
+                    tr[2] += bu * bu;
+                }
+                tr[3] = nanmax(tr[3], fabs(rk[i] / yc[i]));
+                tr[4] = nanmax(tr[4], fabs(rk[i]));
+            }
+            st64<W>(r64 + k, rk);
         }
-        return allreduce<3, 2>(tr, w.partials, parity, w.bar, P.spin_limit, abort_flag, sh);
+        return allreduce<3, 2>(tr, w.partials, parity, w.bar, P.spin_limit, abort_flag, sh, team);
     };
 
     int it = 0, nref = 0, status = kErrNotConverged;
@@ -178,33 +270,87 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_pcg(SolveParams P, Workspa
 
         while (true) {
             // ---- S: p = r + beta p_old ; q = A^ p ; p.q ------------------------------
-            const R* pold = pb[cur];
-            R* pnew = pb[cur ^ 1];
+            const R* __restrict__ pold = pb[cur];
+            R* __restrict__ pnew = pb[cur ^ 1];
             const R rb = static_cast<R>(beta);
             const R rsc = static_cast<R>(scale);
             double v1[1] = {0.0};
-            for (int k = tid; k < N; k += stride) {
-                auto pv = [&](int m) -> R {
-                    R rm;
-                    if (MIXED && from64) rm = static_cast<R>(__ldcg(r64 + m)) * rsc;
-                    else rm = __ldcg(r + m);
-                    return use_p ? rm + rb * __ldcg(pold + m) : rm;
-                };
-                const R pk = pv(k);
-                R acc = pk;
-                if (k > 0) acc -= cW[k] * pv(k - 1);
-                if (k + 1 < N) acc -= cW[k + 1] * pv(k + 1);
-                if (k >= nx) acc -= cS[k] * pv(k - nx);
-                if (k + nx < N) acc -= cS[k + nx] * pv(k + nx);
-                pnew[k] = pk;
-                q[k] = acc;
+            for (int c = tid; c < nchunk; c += stride) {
+                const int k = c * W;
+                const bool hs = k >= nx, hn = k + nx < N, hw = k > 0, he = k + W < N;
+                // r on the cells and their west, east, south and north neighbours
+                R rc[W], rs[W], rn[W], rw = R(0), re = R(0);
+                R pc[W], ps[W], pn[W], pw = R(0), pe = R(0);
+#pragma unroll
+                for (int i = 0; i < W; i++) rs[i] = rn[i] = pc[i] = ps[i] = pn[i] = R(0);
                 if (MIXED && from64) {
-                    r[k] = static_cast<R>(__ldcg(r64 + k)) * rsc;
-                    d[k] = R(0);
+                    double t[W];
+                    ld64<W>(r64 + k, t);
+#pragma unroll
+                    for (int i = 0; i < W; i++) rc[i] = static_cast<R>(t[i]) * rsc;
+                    if (hs) {
+                        ld64<W>(r64 + k - nx, t);
+#pragma unroll
+                        for (int i = 0; i < W; i++) rs[i] = static_cast<R>(t[i]) * rsc;
+                    }
+                    if (hn) {
+                        ld64<W>(r64 + k + nx, t);
+#pragma unroll
+                        for (int i = 0; i < W; i++) rn[i] = static_cast<R>(t[i]) * rsc;
+                    }
+                    if (hw) rw = static_cast<R>(__ldcg(r64 + k - 1)) * rsc;
+                    if (he) re = static_cast<R>(__ldcg(r64 + k + W)) * rsc;
+                } else {
+                    ldv<R, W>(r + k, rc);
+                    if (hs) ldv<R, W>(r + k - nx, rs);
+                    if (hn) ldv<R, W>(r + k + nx, rn);
+                    if (hw) rw = __ldcg(r + k - 1);
+                    if (he) re = __ldcg(r + k + W);
                 }
-                v1[0] += static_cast<double>(pk) * static_cast<double>(acc);
+                if (use_p) {
+                    ldv<R, W>(pold + k, pc);
+                    if (hs) ldv<R, W>(pold + k - nx, ps);
+                    if (hn) ldv<R, W>(pold + k + nx, pn);
+                    if (hw) pw = __ldcg(pold + k - 1);
+                    if (he) pe = __ldcg(pold + k + W);
+                }
+                R cw[W], cs[W], csn[W], cwe = R(0);
+#pragma unroll
+                for (int i = 0; i < W; i++) csn[i] = R(0);
+                ldv<R, W>(cW + k, cw);
+                ldv<R, W>(cS + k, cs);
+                if (he) cwe = cW[k + W];
+                if (hn) ldv<R, W>(cS + k + nx, csn);
+                // p = r + beta p_old on the cells and their neighbours (zero off the grid)
+                R p[W], pS[W], pN[W];
+                const R pW = use_p ? rw + rb * pw : rw;
+                const R pE = use_p ? re + rb * pe : re;
+#pragma unroll
+                for (int i = 0; i < W; i++) {
+                    p[i] = use_p ? rc[i] + rb * pc[i] : rc[i];
+                    pS[i] = use_p ? rs[i] + rb * ps[i] : rs[i];
+                    pN[i] = use_p ? rn[i] + rb * pn[i] : rn[i];
+                }
+                R qv[W];
+#pragma unroll
+                for (int i = 0; i < W; i++) {
+                    const R left = i == 0 ? pW : p[i - 1];
+                    const R right = i == W - 1 ? pE : p[i + 1];
+                    const R cright = i == W - 1 ? cwe : cw[i + 1];
+                    qv[i] = p[i] - cw[i] * left - cright * right - cs[i] * pS[i] - csn[i] * pN[i];
+                    v1[0] += static_cast<double>(p[i]) * static_cast<double>(qv[i]);
+                }
+                stv<R, W>(pnew + k, p);
+                stv<R, W>(q + k, qv);
+                if (MIXED && from64) {
+                    R zero[W];
+#pragma unroll
+                    for (int i = 0; i < W; i++) zero[i] = R(0);
+                    stv<R, W>(r + k, rc);
+                    stv<R, W>(d + k, zero);
+                }
             }
-            if (!allreduce<1, 0>(v1, w.partials, parity, w.bar, P.spin_limit, abort_flag, sh)) {
+            if (!allreduce<1, 0>(v1, w.partials, parity, w.bar, P.spin_limit, abort_flag, sh, team)) {
                 timed_out = true;
                 break;
             }
@@ -217,22 +363,24 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_pcg(SolveParams P, Workspa
             // ---- U: x += alpha p ; r -= alpha q ; r.r --------------------------------
             double v2[2] = {0.0, 0.0};
             const R ra = static_cast<R>(alpha);
-            for (int k = tid; k < N; k += stride) {
-                const R pk = __ldcg(pnew + k);
-                const R qk = __ldcg(q + k);
-                const R rk = __ldcg(r + k) - ra * qk;
-                r[k] = rk;
-                if constexpr (MIXED) {
-                    d[k] = __ldcg(d + k) + ra * pk;
-                    v2[0] += static_cast<double>(rk) * static_cast<double>(rk);
-                } else {
-                    const double yk = __ldcg(y + k) + alpha * pk;
-                    y[k] = yk;
-                    v2[0] += rk * rk;
-                    v2[1] = nanmax(v2[1], fabs(rk / yk));
+            for (int c = tid; c < nchunk; c += stride) {
+                const int k = c * W;
+                R pk[W], qk[W], rk[W], xk[W];
+                ldv<R, W>(pnew + k, pk);
+                ldv<R, W>(q + k, qk);
+                ldv<R, W>(r + k, rk);
+                ldv<R, W>(d + k, xk);
+#pragma unroll
+                for (int i = 0; i < W; i++) {
+                    rk[i] = rk[i] - ra * qk[i];
+                    xk[i] = xk[i] + ra * pk[i];
+                    v2[0] += static_cast<double>(rk[i]) * static_cast<double>(rk[i]);
+                    if constexpr (!MIXED) v2[1] = nanmax(v2[1], fabs(rk[i] / xk[i]));
                 }
+                stv<R, W>(r + k, rk);
+                stv<R, W>(d + k, xk);
             }
-            if (!allreduce<1, 1>(v2, w.partials, parity, w.bar, P.spin_limit, abort_flag, sh)) {
+            if (!allreduce<1, 1>(v2, w.partials, parity, w.bar, P.spin_limit, abort_flag, sh, team)) {
                 timed_out = true;
                 break;
             }
@@ -251,11 +399,21 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_pcg(SolveParams P, Workspa
             // ---- FP64 residual (refinement) -----------------------------------------
             if constexpr (MIXED) {
                 const double inv = 1.0 / scale;
-                for (int k = tid; k < N; k += stride) {
-                    y[k] = __ldcg(y + k) + static_cast<double>(__ldcg(d + k)) * inv;
-                    d[k] = R(0);
+                for (int c = tid; c < nchunk; c += stride) {
+                    const int k = c * W;
+                    double yk[W];
+                    R dk[W], zero[W];
+                    ld64<W>(y + k, yk);
+                    ldv<R, W>(d + k, dk);
+#pragma unroll
+                    for (int i = 0; i < W; i++) {
+                        yk[i] += static_cast<double>(dk[i]) * inv;
+                        zero[i] = R(0);
+                    }
+                    st64<W>(y + k, yk);
+                    stv<R, W>(d + k, zero);
                 }
-                if (!grid_barrier(w.bar, gridDim.x, P.spin_limit, abort_flag)) { timed_out = true; break; }
+                if (!team_barrier(w.bar, team, P.spin_limit, abort_flag)) { timed_out = true; break; }
             }
             if (!true_residual(false)) { timed_out = true; break; }
             nref++;
@@ -291,7 +449,7 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_pcg(SolveParams P, Workspa
 done:
     if (timed_out) {
         if (threadIdx.x == 0) atomicExch(&ctl->status, kErrTimeout);
-        return;
+        return false;
     }
     if (tid == 0) {
         ctl->status = status;
@@ -299,6 +457,62 @@ done:
         ctl->refinements = nref;
         ctl->crit = crit;
         ctl->l2 = l2;
+    }
+    return true;
+}
+
+template <bool MIXED>
+__device__ __forceinline__ bool pcg_solve(const SolveParams& P, const Workspace& w, Team team, RedShared& sh) {
+    constexpr int WV = MIXED ? 4 : 2;
+    if (P.nx % WV == 0) return pcg_solve_w<MIXED, WV>(P, w, team, sh);
+    return pcg_solve_w<MIXED, 1>(P, w, team, sh);
+}
+
+// out-of-line copies for the batched kernel, which holds all four variants: separate
+// functions keep each variant's registers to itself
+template <bool MIXED, int W>
+__device__ __noinline__ bool pcg_solve_call(const SolveParams& P, const Workspace& w, Team team, RedShared& sh) {
+    return pcg_solve_w<MIXED, W>(P, w, team, sh);
+}
+
+template <bool MIXED>
+__device__ __forceinline__ bool pcg_solve_outlined(const SolveParams& P, const Workspace& w, Team team,
+                                                   RedShared& sh) {
+    constexpr int WV = MIXED ? 4 : 2;
+    if (P.nx % WV == 0) return pcg_solve_call<MIXED, WV>(P, w, team, sh);
+    return pcg_solve_call<MIXED, 1>(P, w, team, sh);
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(kSolveThreads, 1) k_pcg(SolveParams P, Workspace w) {
+    __shared__ RedShared sh;
+    pcg_solve<MIXED>(P, w, Team{static_cast<int>(blockIdx.x), static_cast<int>(gridDim.x)}, sh);
+}
+
+// Batched persistent solve: the co-resident grid is split into teams; the leader block
+// of a team takes the next problem of the team's class from the class queue, the team
+// solves it, and repeats until the queue is empty.  Teams synchronise only among
+// themselves, so small problems (one-block teams) never touch an inter-block barrier.
+__global__ void __launch_bounds__(kSolveThreads, 1) kb_pcg(BatchArgs a) {
+    __shared__ RedShared sh;
+    __shared__ int s_idx;
+    const int tm = a.block_team[blockIdx.x];
+    const Team team{static_cast<int>(blockIdx.x) - a.team_first[tm], a.team_size[tm]};
+    const int c = a.team_class[tm];
+    const int qlen = a.class_start[c + 1] - a.class_start[c];
+    unsigned* tbar = a.team_bar + tm;
+    while (true) {
+        if (team.rank == 0 && threadIdx.x == 0) a.team_slot[tm] = atomicAdd(a.queue_head + c, 1);
+        if (!team_barrier(tbar, team, a.spin_limit, a.abort_flag)) return;
+        if (threadIdx.x == 0) s_idx = __ldcg(a.team_slot + tm);
+        // every block of the team has read the slot before the leader may overwrite it
+        if (!team_barrier(tbar, team, a.spin_limit, a.abort_flag)) return;
+        const int idx = s_idx;
+        if (idx >= qlen) return;
+        const ProbDesc& d = a.desc[a.queue[a.class_start[c] + idx]];
+        const bool ok = d.sp.mixed ? pcg_solve_outlined<true>(d.solve, d.w, team, sh)
+                                   : pcg_solve_outlined<false>(d.solve, d.w, team, sh);
+        if (!ok) return;
     }
 }
 
@@ -309,6 +523,28 @@ int solve_max_blocks_per_sm() {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pcg<true>, kSolveThreads, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pcg<false>, kSolveThreads, 0);
     return a < b ? a : b;
+}
+
+int batch_solve_max_blocks_per_sm() {
+    int a = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, kb_pcg, kSolveThreads, 0);
+    return a;
+}
+
+cudaError_t launch_batch_solve(const BatchArgs& a, int grid, cudaStream_t st) {
+    BatchArgs ac = a;
+    void* args[] = {&ac};
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kSolveThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, reinterpret_cast<const void*>(kb_pcg), args);
 }
 
 cudaError_t launch_solve(const SolveParams& p, const Workspace& w, int grid, cudaStream_t st) {

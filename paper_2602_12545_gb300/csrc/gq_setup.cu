@@ -38,11 +38,17 @@ __device__ __forceinline__ double block_sum(double v) {
     return t;   // valid in thread 0
 }
 
+}  // namespace
+
+// Each body below processes one problem with nblk blocks, this block being number blk;
+// the single-problem kernels pass (blockIdx.x, gridDim.x), the batched kernels the
+// block's rank within its problem.
+
 // K1a: per-cell coupling coefficients, input validation, energy before the step
-__global__ void __launch_bounds__(kSetupThreads) k_cells(StepParams sp, DeviceGeometry g, Workspace w) {
+__device__ void cells_body(const StepParams& sp, const DeviceGeometry& g, const Workspace& w, int blk, int nblk) {
     double eloc = 0.0;
     int flags = 0;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < sp.N; k += gridDim.x * blockDim.x) {
+    for (int k = blk * blockDim.x + threadIdx.x; k < sp.N; k += nblk * blockDim.x) {
         const double rho = sp.rho[k], e = sp.eg[k], E = sp.E[k];
         if (!(isfinite(rho) && isfinite(e) && isfinite(E))) flags |= 2;
         else if (!(rho > 0.0 && e > 0.0 && E > 0.0)) flags |= 1;
@@ -65,8 +71,10 @@ __global__ void __launch_bounds__(kSetupThreads) k_cells(StepParams sp, DeviceGe
     }
     if (flags) atomicOr(&w.ctl->input_flags, flags);
     const double t = block_sum<kSetupThreads>(eloc);
-    if (threadIdx.x == 0) w.epart[blockIdx.x] = t;
+    if (threadIdx.x == 0) w.epart[blk] = t;
 }
+
+namespace {
 
 // weight of an interior face between cells a (lower coordinate) and b
 __device__ __forceinline__ double face_weight(double sa, double sb, double Ea, double Eb, double th,
@@ -87,11 +95,13 @@ __device__ __forceinline__ double milne_weight(double s, double h, double geo, i
     return dt * geo * D / (1.0 + kk);
 }
 
+}  // namespace
+
 // K1b: face weights (each cell owns its west and south faces; boundary faces are
 // folded into the cell's diagonal)
-__global__ void __launch_bounds__(kSetupThreads) k_faces(StepParams sp, DeviceGeometry g, Workspace w) {
+__device__ void faces_body(const StepParams& sp, const DeviceGeometry& g, const Workspace& w, int blk, int nblk) {
     const int nx = sp.nx, ny = sp.ny;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < sp.N; k += gridDim.x * blockDim.x) {
+    for (int k = blk * blockDim.x + threadIdx.x; k < sp.N; k += nblk * blockDim.x) {
         const int j = k / nx, i = k - j * nx;
         const double sk = w.sig[k], Ek = sp.E[k];
         double ww = 0.0, ws = 0.0, wb = 0.0;
@@ -114,9 +124,9 @@ __global__ void __launch_bounds__(kSetupThreads) k_faces(StepParams sp, DeviceGe
 }
 
 // K1c: diagonal of the reduced system and its Jacobi scale s = diag^{-1/2} (in place of dloc)
-__global__ void __launch_bounds__(kSetupThreads) k_diag(StepParams sp, Workspace w) {
+__device__ void diag_body(const StepParams& sp, const Workspace& w, int blk, int nblk) {
     const int nx = sp.nx, ny = sp.ny;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < sp.N; k += gridDim.x * blockDim.x) {
+    for (int k = blk * blockDim.x + threadIdx.x; k < sp.N; k += nblk * blockDim.x) {
         const int j = k / nx, i = k - j * nx;
         double d = w.dloc[k] + w.wB[k] + w.wW[k] + w.wS[k];
         if (i < nx - 1) d += w.wW[k + 1];
@@ -126,10 +136,10 @@ __global__ void __launch_bounds__(kSetupThreads) k_diag(StepParams sp, Workspace
 }
 
 // K1d: scaled system  A^ = S A S (unit diagonal), b^ = S b, y0 = E^n / s; FP32 copies
-__global__ void __launch_bounds__(kSetupThreads) k_scale(StepParams sp, Workspace w) {
+__device__ void scale_body(const StepParams& sp, const Workspace& w, int blk, int nblk) {
     const int nx = sp.nx;
     const double* s = w.dloc;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < sp.N; k += gridDim.x * blockDim.x) {
+    for (int k = blk * blockDim.x + threadIdx.x; k < sp.N; k += nblk * blockDim.x) {
         const int j = k / nx, i = k - j * nx;
         const double sk = s[k];
         const double cw = i > 0 ? w.wW[k] * sk * s[k - 1] : 0.0;
@@ -147,13 +157,15 @@ __global__ void __launch_bounds__(kSetupThreads) k_scale(StepParams sp, Workspac
 
 // K6: back-substitution T^{n+1} = tA + tB E^{n+1}, e_g^{n+1} = e_g + C_V (T^{n+1} - T^n),
 // energy after the step
-__global__ void __launch_bounds__(kSetupThreads) k_backsub(StepParams sp, DeviceGeometry g, Workspace w) {
+__device__ void backsub_body(const StepParams& sp, const DeviceGeometry& g, const Workspace& w, int blk,
+                             int nblk) {
     const SolveCtl* ctl = w.ctl;
-    const int st = ctl->status;
-    const bool write = (st == kOk || st == kErrNotConverged) && ctl->abort == 0 && ctl->input_flags == 0;
+    const int st = __ldcg(&ctl->status);
+    const bool write = (st == kOk || st == kErrNotConverged) && __ldcg(&ctl->abort) == 0 &&
+                       __ldcg(&ctl->input_flags) == 0;
     double eloc = 0.0;
     if (write) {
-        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < sp.N; k += gridDim.x * blockDim.x) {
+        for (int k = blk * blockDim.x + threadIdx.x; k < sp.N; k += nblk * blockDim.x) {
             const double En = w.dloc[k] * w.y[k];
             const double Tn = w.tA[k] + w.tB[k] * En;
             const double e = sp.eg[k];
@@ -166,11 +178,11 @@ __global__ void __launch_bounds__(kSetupThreads) k_backsub(StepParams sp, Device
         }
     }
     const double t = block_sum<kSetupThreads>(eloc);
-    if (threadIdx.x == 0) w.epart[gridDim.x + blockIdx.x] = t;
+    if (threadIdx.x == 0) w.epart[nblk + blk] = t;
 }
 
-// deterministic final sums of the energy partials
-__global__ void __launch_bounds__(kSetupThreads) k_finalize(Workspace w, int nblk) {
+// deterministic final sums of the energy partials (one block per problem)
+__device__ void finalize_body(const Workspace& w, int nblk) {
     double a = 0.0, b = 0.0;
     for (int t = threadIdx.x; t < nblk; t += blockDim.x) {
         a += w.epart[t];
@@ -184,6 +196,83 @@ __global__ void __launch_bounds__(kSetupThreads) k_finalize(Workspace w, int nbl
     }
 }
 
+namespace {
+
+__global__ void __launch_bounds__(kSetupThreads) k_cells(StepParams sp, DeviceGeometry g, Workspace w) {
+    cells_body(sp, g, w, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kSetupThreads) k_faces(StepParams sp, DeviceGeometry g, Workspace w) {
+    faces_body(sp, g, w, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kSetupThreads) k_diag(StepParams sp, Workspace w) {
+    diag_body(sp, w, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kSetupThreads) k_scale(StepParams sp, Workspace w) {
+    scale_body(sp, w, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kSetupThreads) k_backsub(StepParams sp, DeviceGeometry g, Workspace w) {
+    backsub_body(sp, g, w, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kSetupThreads) k_finalize(Workspace w, int nblk) { finalize_body(w, nblk); }
+
+// ---- batched variants: one launch covers every problem of a batch ---------------------
+
+// problem p of block b: setup_prefix[p] <= b < setup_prefix[p+1] (binary search)
+__device__ __forceinline__ int problem_of_block(const int* prefix, int n, int b) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(prefix + mid) <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// reset every problem's control block and barrier (status: not solved yet)
+__global__ void kb_init(BatchArgs a) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += gridDim.x * blockDim.x) {
+        const Workspace& w = a.desc[p].w;
+        SolveCtl c{};
+        c.status = kPending;
+        *w.ctl = c;
+        w.bar[0] = 0u;
+        w.bar[1] = 0u;
+    }
+}
+
+__global__ void __launch_bounds__(kSetupThreads) kb_cells(BatchArgs a) {
+    const int p = problem_of_block(a.setup_prefix, a.n, blockIdx.x);
+    const ProbDesc& d = a.desc[p];
+    cells_body(d.sp, d.g, d.w, blockIdx.x - a.setup_prefix[p], d.setup_blocks);
+}
+__global__ void __launch_bounds__(kSetupThreads) kb_faces(BatchArgs a) {
+    const int p = problem_of_block(a.setup_prefix, a.n, blockIdx.x);
+    const ProbDesc& d = a.desc[p];
+    faces_body(d.sp, d.g, d.w, blockIdx.x - a.setup_prefix[p], d.setup_blocks);
+}
+__global__ void __launch_bounds__(kSetupThreads) kb_diag(BatchArgs a) {
+    const int p = problem_of_block(a.setup_prefix, a.n, blockIdx.x);
+    const ProbDesc& d = a.desc[p];
+    diag_body(d.sp, d.w, blockIdx.x - a.setup_prefix[p], d.setup_blocks);
+}
+__global__ void __launch_bounds__(kSetupThreads) kb_scale(BatchArgs a) {
+    const int p = problem_of_block(a.setup_prefix, a.n, blockIdx.x);
+    const ProbDesc& d = a.desc[p];
+    scale_body(d.sp, d.w, blockIdx.x - a.setup_prefix[p], d.setup_blocks);
+}
+__global__ void __launch_bounds__(kSetupThreads) kb_backsub(BatchArgs a) {
+    const int p = problem_of_block(a.setup_prefix, a.n, blockIdx.x);
+    const ProbDesc& d = a.desc[p];
+    backsub_body(d.sp, d.g, d.w, blockIdx.x - a.setup_prefix[p], d.setup_blocks);
+}
+// one block per problem: energy sums, then gather the control block
+__global__ void __launch_bounds__(kSetupThreads) kb_finalize(BatchArgs a) {
+    const ProbDesc& d = a.desc[blockIdx.x];
+    finalize_body(d.w, d.setup_blocks);
+    __syncthreads();
+    if (threadIdx.x == 0) a.ctl_out[blockIdx.x] = *d.w.ctl;
+}
+
 }  // namespace
 
 cudaError_t launch_setup(const StepParams& sp, const DeviceGeometry& g, const Workspace& w, int nblk,
@@ -192,6 +281,21 @@ cudaError_t launch_setup(const StepParams& sp, const DeviceGeometry& g, const Wo
     k_faces<<<nblk, kSetupThreads, 0, st>>>(sp, g, w);
     k_diag<<<nblk, kSetupThreads, 0, st>>>(sp, w);
     k_scale<<<nblk, kSetupThreads, 0, st>>>(sp, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_setup(const BatchArgs& a, int total, cudaStream_t st) {
+    kb_init<<<(a.n + 127) / 128, 128, 0, st>>>(a);
+    kb_cells<<<total, kSetupThreads, 0, st>>>(a);
+    kb_faces<<<total, kSetupThreads, 0, st>>>(a);
+    kb_diag<<<total, kSetupThreads, 0, st>>>(a);
+    kb_scale<<<total, kSetupThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_finish(const BatchArgs& a, int total, cudaStream_t st) {
+    kb_backsub<<<total, kSetupThreads, 0, st>>>(a);
+    kb_finalize<<<a.n, kSetupThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -140,3 +140,95 @@ def step_problem(plan: FLDPlan, p: FLDProblem, rho, e_g, E_r, T_out=None, *, pre
                          rtol=p.rtol if rtol is None else rtol, **kw)
     return plan.step(rho, e_g, E_r, T_out, opacity_R=p.opacity_R, opacity_P=p.opacity_P, gamma=p.gamma,
                      mu=p.mu, dt=p.dt, bc=p.bc, opts=opts, check=check)
+
+
+class FLDBatch:
+    """gq_batch_*: independent problems (each with its own FLDPlan) stepped together in one
+    persistent launch, replayed from a CUDA graph."""
+
+    def __init__(self, plans, cells_per_block: int = 0, max_team: int = 0, use_graph: bool = True):
+        L = N.load()
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
+        o = N.BatchOpts()
+        L.gq_batch_opts_default(ctypes.byref(o))
+        o.cells_per_block, o.max_team, o.use_graph = int(cells_per_block), int(max_team), int(bool(use_graph))
+        h = ctypes.c_void_p()
+        rc = L.gq_batch_create(ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)), len(self.plans), ctypes.byref(o),
+                               ctypes.byref(h))
+        if rc != N.GQ_OK:
+            raise N.GQError(rc, "gq_batch_create")
+        self._h = h
+        self._keep = None
+
+    def _items(self, problems, fields, opts_list):
+        items = (N.BatchItem * len(self.plans))()
+        for i, (P, (rho, e_g, E, T), o) in enumerate(zip(problems, fields, opts_list)):
+            plan = self.plans[i]
+            for t, n in ((rho, "rho"), (e_g, "e_g"), (E, "E_r")):
+                plan._check(t, n)
+            if T is not None:
+                plan._check(T, "T_out")
+            it = items[i]
+            it.rho, it.e_g, it.E_r = rho.data_ptr(), e_g.data_ptr(), E.data_ptr()
+            it.T_g_out = T.data_ptr() if T is not None else None
+            it.opacity = N.OpacityLaw(*[float(v) for v in tuple(P.opacity_R) + tuple(P.opacity_P)])
+            it.eos = N.Eos(float(P.gamma), float(P.mu))
+            it.dt = float(P.dt)
+            for s in range(4):
+                it.bc.side[s] = int(P.bc[s])
+            it.opts = o.to_c()
+        return items
+
+    @staticmethod
+    def default_opts(problems, **kw):
+        return [SolverOptions(prec=P.precision, limiter=P.limiter, rtol=P.rtol, **kw) for P in problems]
+
+    def step(self, problems, fields, opts_list=None, stream=None, check=True):
+        """One step of every problem; fields is a list of (rho, e_g, E_r, T_out) tensors."""
+        opts_list = opts_list or self.default_opts(problems)
+        items = self._items(problems, fields, opts_list)
+        infos = (N.StepInfo * len(self.plans))()
+        st = (stream or torch.cuda.current_stream()).cuda_stream
+        rc = N.load().gq_batch_step(self._h, items, ctypes.c_void_p(st), infos)
+        out = [i.as_dict() for i in infos]
+        if check and rc != N.GQ_OK:
+            raise N.GQError(rc, "gq_batch_step")
+        return rc, out
+
+    def autotune(self, problems, fields, opts_list=None, stream=None):
+        opts_list = opts_list or self.default_opts(problems)
+        items = self._items(problems, fields, opts_list)
+        best = N.BatchOpts()
+        ms = ctypes.c_double()
+        st = (stream or torch.cuda.current_stream()).cuda_stream
+        rc = N.load().gq_batch_autotune(self._h, items, ctypes.c_void_p(st), ctypes.byref(best), ctypes.byref(ms))
+        if rc != N.GQ_OK:
+            raise N.GQError(rc, "gq_batch_autotune")
+        return {"cells_per_block": best.cells_per_block, "max_team": best.max_team, "ms": ms.value}
+
+    def reschedule(self, cells_per_block=0, max_team=0, use_graph=True):
+        o = N.BatchOpts()
+        o.cells_per_block, o.max_team, o.use_graph = int(cells_per_block), int(max_team), int(bool(use_graph))
+        rc = N.load().gq_batch_reschedule(self._h, ctypes.byref(o))
+        if rc != N.GQ_OK:
+            raise N.GQError(rc, "gq_batch_reschedule")
+
+    @property
+    def last_ms(self) -> float:
+        return float(N.load().gq_batch_last_step_ms(self._h))
+
+    @property
+    def uses_graph(self) -> bool:
+        return bool(N.load().gq_batch_uses_graph(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            N.load().gq_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

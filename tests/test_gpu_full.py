@@ -1,0 +1,58 @@
+"""Full-size parity: the 1024 x 1024 geometric Cartesian workload (FP64 path, 1e-10) and the
+2048 x 1024 spherical-polar workload (mixed path, 1e-8) against the oracle's own CG solve,
+every cell compared, in the launch configuration the benchmark times.  The oracle solves
+take a minute or two of host time each."""
+import numpy as np
+import pytest
+
+from paper_2602_12545_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fld():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2602_12545_gb300 import build
+    build.build()
+    from paper_2602_12545_gb300 import fld as F
+    return F
+
+
+def run(F, P, prec, rtol):
+    plan = F.FLDPlan.for_problem(P)
+    rho, e_g, E, T = F.device_fields(P)
+    info = F.step_problem(plan, P, rho, e_g, E, T, prec=prec, rtol=rtol)
+    out = {"E_r": E.cpu().numpy(), "T_g": T.cpu().numpy(), "e_g": e_g.cpu().numpy(), "info": info}
+    plan.close()
+    return out
+
+
+def errors(out, ref):
+    return {f: float(np.max(np.abs(out[f] - ref[f]) / np.abs(ref[f]))) for f in ("E_r", "T_g", "e_g")}
+
+
+def test_config1_fp64_full(fld, orc):
+    P = W.config1()
+    ref = orc.step(P, "cg", tol=1e-15)
+    assert ref["cell_residual"] < 1e-12
+    out = run(fld, P, W.PREC_FP64, 1e-12)
+    assert out["info"]["status"] == 0, out["info"]
+    err = errors(out, ref)
+    print("config1 fp64", err, out["info"]["iterations"])
+    assert max(err.values()) <= 1e-10, err
+
+
+def test_config2_mixed_full(fld, orc):
+    P = W.config2()
+    ref = orc.step(P, "cg", tol=1e-15)
+    assert ref["cell_residual"] < 1e-12
+    out = run(fld, P, W.PREC_MIXED, 1e-11)
+    assert out["info"]["status"] == 0, out["info"]
+    err = errors(out, ref)
+    print("config2 mixed", err, out["info"]["iterations"], out["info"]["refinements"])
+    assert max(err.values()) <= 1e-8, err
+    e0, e1 = out["info"]["energy_before"], out["info"]["energy_after"]
+    assert e1 < e0      # Milne outer boundary: energy leaves the grid
