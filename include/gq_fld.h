@@ -133,6 +133,10 @@ gq_status gq_fld_setup(const gq_grid_desc *grid, gq_fld_plan **out);
 /* Device bytes held by a plan (geometry and workspace). */
 size_t gq_fld_plan_bytes(const gq_fld_plan *plan);
 
+/* Device bytes gq_fld_setup would allocate for an nx x ny grid on the current device
+ * (0 for invalid sizes or when no device is available).  Allocates nothing. */
+size_t gq_fld_plan_bytes_for(int nx, int ny);
+
 /* One implicit FLD step (Sec. 3.2.1, a single sub-cycle, n_sub = 1): face coefficients,
  * C_V, the phi / psi coefficients, the reduced system, its Krylov solve and T^{n+1}.
  *   rho      [ny][nx] device, g/cm^3, > 0, read only.
@@ -228,6 +232,79 @@ void gq_batch_destroy(gq_batch *batch);
 /* One batched step without keeping a batch (no graph): create, step, destroy. */
 gq_status gq_fld_step_batched(gq_fld_plan *const *plans, int n, const gq_batch_item *items, void *stream,
                               gq_step_info *infos);
+
+/* ---------------------------------------------------------------------------------------
+ * Serving: a continuous-batching request loop.  Requests (a grid, initial fields and a
+ * number of consecutive implicit steps) are queued with host copies of their inputs.
+ * Each engine tick (gq_server_poll) admits queued requests in arrival order while their
+ * device footprint fits the memory budget, keeps admitted requests' state resident on
+ * the device, steps every resident request once in one batched launch, and retires the
+ * finished ones (results copied to the caller's host buffers, memory returned).  Not in
+ * the paper.
+ * --------------------------------------------------------------------------------------- */
+
+typedef struct {
+    size_t budget_bytes;   /* device bytes resident requests may hold (plans + fields), > 0 */
+    int max_active;        /* most requests resident and stepped together (0 = 256) */
+    int use_graph;         /* 1: replay a captured graph while the resident set is unchanged */
+    int reserved[6];
+} gq_server_opts;
+
+typedef struct {
+    gq_grid_desc grid;                      /* host geometry, copied at submit */
+    const double *rho, *e_g, *E_r;          /* host initial fields [ny][nx], copied at submit */
+    gq_opacity_law opacity;
+    gq_eos eos;
+    double dt;                              /* per step */
+    gq_bc bc;
+    gq_solver_opts opts;
+    int n_steps;                            /* consecutive implicit steps, >= 1 */
+    double *E_r_out, *e_g_out, *T_g_out;    /* host buffers [ny][nx] filled at completion (may be NULL) */
+} gq_request;
+
+typedef struct {
+    int state;                 /* 0 queued, 1 resident, 2 done */
+    int status;                /* gq_status (GQ_OK until a step fails) */
+    int steps_done;
+    int iterations;            /* Krylov iterations summed over the request's steps */
+    double submit_s, admit_s, done_s;   /* host steady-clock seconds */
+    double energy_before;      /* sum V (E + e_g) before the first step */
+    double energy_after;       /* and after the last */
+    size_t device_bytes;       /* resident footprint */
+    int reserved[4];
+} gq_request_info;
+
+typedef struct gq_server gq_server;
+
+/* Create a server on the current device.  Errors: GQ_ERR_INVALID_ARG, GQ_ERR_OOM, GQ_ERR_CUDA. */
+gq_status gq_server_create(const gq_server_opts *opts, gq_server **out);
+
+/* Device bytes a request of an nx x ny grid holds while resident (plan arena + fields). */
+size_t gq_server_request_bytes(int nx, int ny);
+
+/* Queue a request (inputs copied; output buffers must stay valid until it is done).
+ * Errors: GQ_ERR_INVALID_ARG, GQ_ERR_BUDGET (the request alone exceeds the budget). */
+gq_status gq_server_submit(gq_server *server, const gq_request *request, int64_t *id);
+
+/* One engine tick: admit, step every resident request once, retire finished ones.
+ * *completed (may be NULL) receives the number of requests finished in this tick.
+ * A request whose step fails finishes with that status; GQ_ERR_CUDA if nothing ran. */
+gq_status gq_server_poll(gq_server *server, int *completed);
+
+/* State and timings of a request (until released). */
+gq_status gq_server_info(gq_server *server, int64_t id, gq_request_info *info);
+
+/* Forget a finished request. */
+gq_status gq_server_release(gq_server *server, int64_t id);
+
+/* Requests queued or resident. */
+int gq_server_pending(gq_server *server);
+
+/* Device bytes held by resident requests. */
+size_t gq_server_used_bytes(gq_server *server);
+
+/* Destroy the server and everything it holds (NULL is ignored). */
+void gq_server_destroy(gq_server *server);
 
 /* Default solver options: FP64, LP limiter, rtol 1e-10, max_iter 200000, inner_rtol 0.1,
  * max_refine 200, default spin limit, keep the search direction. */

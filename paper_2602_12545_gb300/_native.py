@@ -70,10 +70,41 @@ class BatchOpts(ctypes.Structure):
                 ("reserved", ctypes.c_int * 5)]
 
 
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_size_t), ("max_active", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("grid", GridDesc), ("rho", _dp), ("e_g", _dp), ("E_r", _dp), ("opacity", OpacityLaw),
+                ("eos", Eos), ("dt", ctypes.c_double), ("bc", Bc), ("opts", SolverOpts), ("n_steps", ctypes.c_int),
+                ("E_r_out", _dp), ("e_g_out", _dp), ("T_g_out", _dp)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int), ("status", ctypes.c_int), ("steps_done", ctypes.c_int),
+                ("iterations", ctypes.c_int), ("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double),
+                ("done_s", ctypes.c_double), ("energy_before", ctypes.c_double), ("energy_after", ctypes.c_double),
+                ("device_bytes", ctypes.c_size_t), ("reserved", ctypes.c_int * 4)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 # every symbol include/gq_fld.h declares, with (restype, argtypes)
 SIGNATURES = {
     "gq_fld_setup": (ctypes.c_int, [ctypes.POINTER(GridDesc), ctypes.POINTER(ctypes.c_void_p)]),
     "gq_fld_plan_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "gq_fld_plan_bytes_for": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int]),
+    "gq_server_create": (ctypes.c_int, [ctypes.POINTER(ServerOpts), ctypes.POINTER(ctypes.c_void_p)]),
+    "gq_server_request_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int]),
+    "gq_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_int64)]),
+    "gq_server_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "gq_server_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(RequestInfo)]),
+    "gq_server_release": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "gq_server_pending": (ctypes.c_int, [ctypes.c_void_p]),
+    "gq_server_used_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "gq_server_destroy": (None, [ctypes.c_void_p]),
     "gq_fld_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.POINTER(OpacityLaw), ctypes.POINTER(Eos),
                                    ctypes.c_double, ctypes.POINTER(Bc), ctypes.POINTER(SolverOpts),

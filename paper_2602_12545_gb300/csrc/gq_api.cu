@@ -172,6 +172,24 @@ void layout(gq_fld_plan* P, Bump& b) {
     w.ctl = b.take<gq::SolveCtl>(1);
 }
 
+// device, launch geometry and arena size of a plan whose nx, ny, N are set
+bool size_plan(gq_fld_plan* P) {
+    if (cudaGetDevice(&P->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const int per_sm = gq::solve_max_blocks_per_sm();
+    if (per_sm < 1) return false;
+    const int need = (P->N + gq::kSolveThreads - 1) / gq::kSolveThreads;
+    P->solve_grid_max = std::max(1, std::min(per_sm * P->num_sms, need));
+    P->setup_blocks = std::max(1, std::min(P->num_sms * 8, (P->N + gq::kSetupThreads - 1) / gq::kSetupThreads));
+    Bump sizing{nullptr, 0};
+    layout(P, sizing);
+    P->arena_bytes = sizing.off + 256;
+    return true;
+}
+
 bool finite_all(const double* v, int n) {
     for (int i = 0; i < n; i++)
         if (!std::isfinite(v[i])) return false;
@@ -306,20 +324,10 @@ gq_status gq_fld_setup(const gq_grid_desc* gd, gq_fld_plan** out) {
     P->ny = gd->ny;
     P->N = gd->nx * gd->ny;
     P->coord = gd->coord;
-    if (cudaGetDevice(&P->device) != cudaSuccess ||
-        cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device) != cudaSuccess) {
+    if (!size_plan(P)) {
         delete P;
         return GQ_ERR_CUDA;
     }
-    const int per_sm = gq::solve_max_blocks_per_sm();
-    if (per_sm < 1) { delete P; return GQ_ERR_CUDA; }
-    const int need = (P->N + gq::kSolveThreads - 1) / gq::kSolveThreads;
-    P->solve_grid_max = std::max(1, std::min(per_sm * P->num_sms, need));
-    P->setup_blocks = std::max(1, std::min(P->num_sms * 8, (P->N + gq::kSetupThreads - 1) / gq::kSetupThreads));
-
-    Bump sizing{nullptr, 0};
-    layout(P, sizing);
-    P->arena_bytes = sizing.off + 256;
     if (cudaMalloc(&P->arena, P->arena_bytes) != cudaSuccess) {
         cudaGetLastError();
         delete P;
@@ -362,6 +370,15 @@ gq_status gq_fld_setup(const gq_grid_desc* gd, gq_fld_plan** out) {
 }
 
 size_t gq_fld_plan_bytes(const gq_fld_plan* P) { return P ? P->arena_bytes : 0; }
+
+size_t gq_fld_plan_bytes_for(int nx, int ny) {
+    if (nx < 1 || ny < 1 || (long long)nx * ny > (1ll << 30)) return 0;
+    gq_fld_plan tmp{};
+    tmp.nx = nx;
+    tmp.ny = ny;
+    tmp.N = nx * ny;
+    return size_plan(&tmp) ? tmp.arena_bytes : 0;
+}
 
 void gq_fld_destroy(gq_fld_plan* P) {
     if (!P) return;

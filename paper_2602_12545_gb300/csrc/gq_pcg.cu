@@ -375,7 +375,10 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
                     rk[i] = rk[i] - ra * qk[i];
                     xk[i] = xk[i] + ra * pk[i];
                     v2[0] += static_cast<double>(rk[i]) * static_cast<double>(rk[i]);
-                    if constexpr (!MIXED) v2[1] = nanmax(v2[1], fabs(rk[i] / xk[i]));
+                    // recursive stop estimate in FP32 (FP64 division is slow on this part;
+                    // the decisive test uses the exact FP64 residual)
+                    if constexpr (!MIXED)
+                        v2[1] = nanmax(v2[1], (double)__fdividef((float)fabs(rk[i]), (float)fabs(xk[i])));
                 }
                 stv<R, W>(r + k, rk);
                 stv<R, W>(d + k, xk);

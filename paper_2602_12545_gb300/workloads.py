@@ -111,7 +111,9 @@ def geometric_faces(n: int, d0: float, ratio: float, x0: float = 0.0) -> np.ndar
 
 
 def log_faces(n: int, r_in: float, r_out: float) -> np.ndarray:
-    return np.exp(np.linspace(math.log(r_in), math.log(r_out), n + 1))
+    f = np.exp(np.linspace(math.log(r_in), math.log(r_out), n + 1))
+    f[0], f[-1] = r_in, r_out
+    return f
 
 
 def theta_faces(n: int) -> np.ndarray:
