@@ -39,6 +39,12 @@ FALLBACK_HBM = 6800.0
 
 # algorithmic bytes per cell (each array touched once per pass)
 BYTES_ITER = {1: 32.0, 0: 64.0}       # 2 coefficients + (x, r, p) read and written
+# one multigrid V-cycle per iteration, per fine cell: 4 level-0 sweeps (value, c_W, c_S
+# in, value out: 16 B each), transfers (t twice, 8 B), z_old read (4 B), times 4/3 for
+# the coarser levels, plus reading z in the direction pass (4 B); the FP64 path also
+# writes the FP32 copy of its residual (4 B)
+BYTES_VCYCLE = (4 * 16 + 8 + 4) * 4.0 / 3.0 + 4
+BYTES_ITER_MG = {1: 32.0 + BYTES_VCYCLE, 0: 64.0 + BYTES_VCYCLE + 4.0}
 BYTES_RESID = {1: 60.0, 0: 40.0}      # FP64 residual (c_W, c_S, b, y in; r out) [+ y += d for mixed]
 KERNELS_PER_STEP = 7                  # cells, faces, diag, scale, pcg, backsub, finalize
 # cell-wise residual target of the spherical workload: the loosest setting whose E and T
@@ -52,8 +58,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["c2", "c1", "c0"], default="c2")
+    ap.add_argument("--workload", choices=["c2", "c1", "c0", "batched", "serving"], default="c2")
+    ap.add_argument("--problems", type=int, default=256, help="batched: number of problems")
+    ap.add_argument("--requests", type=int, default=400, help="serving: requests in the trace")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serving: mean arrival rate (1/s)")
+    ap.add_argument("--budget-gb", type=float, default=60.0, help="serving: device memory budget")
     ap.add_argument("--rtol", type=float, default=None)
+    ap.add_argument("--precond", type=int, default=1, help="1 multigrid V-cycle (default), 0 Jacobi")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison path")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
@@ -227,7 +238,7 @@ def run_ours(args):
         info["ms"] = s0.elapsed_time(s1)
         return info
 
-    opts = F.SolverOptions(prec=prec, limiter=P.limiter, rtol=rtol, timing=1)
+    opts = F.SolverOptions(prec=prec, limiter=P.limiter, rtol=rtol, timing=1, precond=args.precond)
     # accuracy reference: FP64 path solved tightly (untimed)
     ref_opts = F.SolverOptions(prec=0, limiter=P.limiter, rtol=1e-13, timing=0, max_iter=1000000)
     ref_info = one(ref_opts, check=False)       # may stop at the FP64 floor (status 4)
@@ -266,7 +277,8 @@ def run_ours(args):
     t_solve = statistics.mean(i["t_solve_ms"] for i in infos)
     t_setup = statistics.mean(i["t_setup_ms"] for i in infos)
     t_finish = statistics.mean(i["t_finish_ms"] for i in infos)
-    alg_bytes = N * (its * BYTES_ITER[prec] + (refs + 1) * BYTES_RESID[prec])
+    b_iter = BYTES_ITER_MG[prec] if args.precond == 1 else BYTES_ITER[prec]
+    alg_bytes = N * (its * b_iter + (refs + 1) * BYTES_RESID[prec])
     achieved = alg_bytes / (t_solve / 1e3) / 1e9
     peak, peak_kind = peaks()
     tag = "pcg_mixed_c2" if (prec == 1 and args.workload == "c2") else f"pcg_{'mixed' if prec else 'fp64'}_{args.workload}"
@@ -277,7 +289,7 @@ def run_ours(args):
     # FP64 GPU path on the same workload and tolerance
     fp64 = None
     if not args.no_fp64 and prec == 1:
-        f_opts = F.SolverOptions(prec=0, limiter=P.limiter, rtol=rtol, timing=1)
+        f_opts = F.SolverOptions(prec=0, limiter=P.limiter, rtol=rtol, timing=1, precond=args.precond)
         one(f_opts)
         f_infos = [one(f_opts) for _ in range(max(1, min(args.steps, 3)))]
         f_ms = statistics.mean(i["ms"] for i in f_infos)
@@ -326,6 +338,7 @@ def run_ours(args):
         "config": {"workload": f"{P.name}_{'mixed' if prec else 'fp64'}", "grid": desc, "nx": P.nx, "ny": P.ny,
                    "cells": N, "precision": "FP32 inner PCG + FP64 refinement" if prec else "FP64 PCG",
                    "rtol": rtol, "residual": "cell-wise max |b-Ax|_k/(A_kk x_k) of the reduced system",
+                   "preconditioner": "aggregation multigrid V-cycle (FP32)" if args.precond == 1 else "Jacobi",
                    "l2": "inputs restored and L2 flushed (512 MiB write) before every step, outside the timed events",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "step_latency_ms": {"p50": p50, "p99": p99},
@@ -337,7 +350,7 @@ def run_ours(args):
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": peak_kind, "traffic": traffic,
                      "algorithmic_bytes_per_launch": alg_bytes,
-                     "bytes_per_cell": {"iteration": BYTES_ITER[prec], "fp64_residual": BYTES_RESID[prec]}},
+                     "bytes_per_cell": {"iteration": b_iter, "fp64_residual": BYTES_RESID[prec]}},
         "fp64_gpu": fp64,
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -352,11 +365,150 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _batch_line(args, world, value, total_ms, infos, extra):
+    statuses = {}
+    for i in infos:
+        statuses[i["status"]] = statuses.get(i["status"], 0) + 1
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", **extra,
+        "status_counts": statuses,
+    }
+
+
+def run_batched(args):
+    """256 independent problems of uneven size (32..512 per side, Cartesian and spherical,
+    dt 1e3..1e6 s) in one persistent launch replayed from a CUDA graph, schedule chosen by
+    the autotuner (untimed, once)."""
+    import numpy as np
+    import torch
+    from paper_2602_12545_gb300 import fld as F
+    from paper_2602_12545_gb300 import workloads as W
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    probs = W.config3(args.problems)
+    plans = [F.FLDPlan.for_problem(P) for P in probs]
+    pristine = [F.device_fields(P) for P in probs]
+    fields = [(r, e.clone(), E.clone(), T.clone()) for (r, e, E, T) in pristine]
+    opts = [F.SolverOptions(prec=1, limiter=P.limiter, rtol=P.rtol, precond=args.precond) for P in probs]
+    B = F.FLDBatch(plans)
+    t_tune = time.perf_counter()
+    tuned = B.autotune(probs, fields, opts)
+    t_tune = time.perf_counter() - t_tune
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def restore():
+        for (r, e, E, T), (r0, e0, E0, T0) in zip(fields, pristine):
+            e.copy_(e0)
+            E.copy_(E0)
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        restore()
+        B.step(probs, fields, opts, check=False)
+    clocks = Clocks(gpu_index(int(os.environ.get("LOCAL_RANK", "0"))))
+    torch.cuda.synchronize()
+    clocks.start()
+    ms, infos = [], None
+    for _ in range(args.steps):
+        restore()
+        rc, infos = B.step(probs, fields, opts, check=False)
+        ms.append(B.last_ms)
+    ck = clocks.stop()
+    total_ms = sum(ms)
+    cells = sum(P.ncells for P in probs)
+    # accuracy on a few members against their own tightly solved FP64 step
+    errs = []
+    for p in range(0, len(probs), max(1, len(probs) // 4)):
+        P = probs[p]
+        r0, e0, E0, T0 = pristine[p]
+        e1, E1, T1 = e0.clone(), E0.clone(), T0.clone()
+        F.step_problem(plans[p], P, r0, e1, E1, T1, prec=0, rtol=1e-13, check=False, precond=args.precond)
+        errs.append(float(((fields[p][2] - E1).abs() / E1.abs()).max()))
+    its = [i["iterations"] for i in infos]
+    line = _batch_line(args, world, world * cells * args.steps / (total_ms / 1e3), total_ms, infos, {
+        "config": {"workload": f"c3_batch{len(probs)}_mixed", "problems": len(probs), "cells": cells,
+                   "sides": "nx, ny log-uniform in [32, 512], Cartesian and spherical-polar alternating",
+                   "rtol": probs[0].rtol, "preconditioner": "multigrid" if args.precond == 1 else "Jacobi",
+                   "l2": "inputs restored and L2 flushed before every step, outside the timed events",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "batch": {"autotuned": tuned, "autotune_s": t_tune, "graph": B.uses_graph,
+                  "iterations_mean": float(np.mean(its)), "iterations_max": int(np.max(its)),
+                  "max_rel_err_E_vs_fp64_tight_sampled": max(errs)},
+        "step_latency_ms": {"p50": statistics.median(ms), "p99": max(ms)},
+        "gpu_launches": 9 * args.steps, "clocks": ck})
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    B.close()
+    for p in plans:
+        p.close()
+
+
+def run_serving(args):
+    """Continuous-batching serving of a finite Poisson trace (square grids 64..2048,
+    10 steps each, memory budget), against the same requests served one at a time on the
+    plain FP64 path."""
+    import numpy as np
+    import torch
+    from paper_2602_12545_gb300 import fld as F
+    from paper_2602_12545_gb300 import serve as S
+    from paper_2602_12545_gb300 import workloads as W
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    trace = W.config4_trace(args.requests, rate_per_s=args.rate)
+    opts = F.SolverOptions(prec=1, limiter=0, rtol=1e-8, precond=args.precond)
+    budget = int(args.budget_gb * (1 << 30))
+    warm = W.config4_trace(4, rate_per_s=args.rate, side_lo=64, side_hi=128, n_steps=2, seed=99)
+    S.run_trace(warm, budget)
+    clocks = Clocks(gpu_index(int(os.environ.get("LOCAL_RANK", "0"))))
+    clocks.start()
+    out = S.run_trace(trace, budget, opts=opts)
+    ck = clocks.stop()
+    # one at a time, plain FP64 path, same requests (a sample of them when the trace is long)
+    sample = trace[: min(len(trace), 40)]
+    t_seq, cells_seq = 0.0, 0
+    for req in sample:
+        P = W.serve_problem(req)
+        plan = F.FLDPlan.for_problem(P)
+        rho, e_g, E, T = F.device_fields(P)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(req.n_steps):
+            F.step_problem(plan, P, rho, e_g, E, T, prec=0, rtol=1e-8, check=False, precond=args.precond)
+        torch.cuda.synchronize()
+        t_seq += time.perf_counter() - t0
+        cells_seq += P.ncells * req.n_steps
+        plan.close()
+    done = out.pop("completed")
+    line = {
+        "metric": METRIC, "value": out["throughput_cell_updates_per_s"], "unit": UNIT, "n_gpus": 1,
+        "steps": args.requests, "warmup": len(warm), "ms_per_step": 1e3 * out["makespan_s"] / max(1, len(done)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"c4_serving_{args.requests}req_{int(args.rate)}per_s", "requests": args.requests,
+                   "rate_per_s": args.rate, "sides": "square, log-uniform in [64, 2048]", "steps_per_request": 10,
+                   "budget_gb": args.budget_gb, "rtol": 1e-8,
+                   "preconditioner": "multigrid" if args.precond == 1 else "Jacobi"},
+        "serving": {k: v for k, v in out.items()},
+        "latency_s": {"p50": out["latency_p50_s"], "p99": out["latency_p99_s"]},
+        "one_at_a_time_fp64": {"value": cells_seq / t_seq, "unit": UNIT, "requests_sampled": len(sample)},
+        "overloaded": out["offered_cell_updates_per_s"] > out["throughput_cell_updates_per_s"],
+        "clocks": ck,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     """The FP64 CPU oracle on the host cores (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
+        return
+    if args.workload in ("batched", "serving"):
+        print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle baseline is defined for the single-grid workloads (c0, c1, c2)"}))
         return
     P, desc = workload(args.workload)
     rtol = args.rtol if args.rtol is not None else (DEFAULT_C2_RTOL if args.workload == "c2" else P.rtol)
@@ -386,6 +538,10 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

@@ -47,6 +47,7 @@ enum { GQ_CARTESIAN = 0, GQ_SPHERICAL_POLAR = 1 };
 enum { GQ_BC_REFLECT = 0, GQ_BC_OUTFLOW_MILNE = 1 };
 enum { GQ_LIMITER_LP = 0, GQ_LIMITER_MINERBO = 1, GQ_LIMITER_NONE = 2 };
 enum { GQ_PREC_FP64 = 0, GQ_PREC_MIXED = 1 };
+enum { GQ_PRECOND_JACOBI = 0, GQ_PRECOND_MG = 1 };
 
 /* Grid geometry (Sec. 3.2.1 and Eq. fldg).  Cartesian (x, y) per unit depth, or
  * axisymmetric spherical-polar (r, theta) with the common factor 2 pi dropped.
@@ -91,7 +92,14 @@ typedef struct { int side[4]; } gq_bc;
  *   restart     mixed only: 1 restarts the Krylov space at every refinement (classical
  *               iterative refinement), 0 keeps the search direction (default).
  *   timing      1 records CUDA events around the set-up, solve and finish phases on the
- *               stream and reports their durations in gq_step_info (0 = off). */
+ *               stream and reports their durations in gq_step_info (0 = off).
+ *   precond     GQ_PRECOND_MG (default): CG preconditioned by one V-cycle of aggregation
+ *               multigrid (2 x 2 Galerkin coarsening of the Jacobi-scaled operator, two
+ *               weighted-Jacobi sweeps before and after, exact solve of the coarsest
+ *               <= 32 cells), in FP32 for both precisions, with Polak-Ribiere directions.
+ *               GQ_PRECOND_JACOBI: diagonal (Jacobi) preconditioning only.
+ *   mg_omega    Jacobi smoothing weight of the V-cycle, in (0, 1] (0 = default 0.8).
+ *   mg_over     coarse-correction factor, in (0, 2) (0 = default 1.5). */
 typedef struct {
     int prec;
     int limiter;
@@ -102,7 +110,11 @@ typedef struct {
     int64_t spin_limit;
     int restart;
     int timing;
-    int reserved[6];
+    int precond;
+    int reserved0;
+    double mg_omega;
+    double mg_over;
+    int reserved[2];
 } gq_solver_opts;
 
 /* Result of one step (host struct). */
@@ -307,7 +319,8 @@ size_t gq_server_used_bytes(gq_server *server);
 void gq_server_destroy(gq_server *server);
 
 /* Default solver options: FP64, LP limiter, rtol 1e-10, max_iter 200000, inner_rtol 0.1,
- * max_refine 200, default spin limit, keep the search direction. */
+ * max_refine 200, default spin limit, keep the search direction, multigrid
+ * preconditioning (omega 0.8, coarse factor 1.5). */
 void gq_solver_opts_default(gq_solver_opts *opts);
 
 /* Static description of a status code. */

@@ -20,6 +20,8 @@ GQ_ERR_NOT_CONVERGED = 4
 GQ_ERR_NONFINITE = 5
 GQ_ERR_TIMEOUT = 6
 GQ_ERR_BUDGET = 7
+GQ_PRECOND_JACOBI = 0
+GQ_PRECOND_MG = 1
 
 _dp = ctypes.POINTER(ctypes.c_double)
 
@@ -45,7 +47,8 @@ class SolverOpts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("limiter", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("inner_rtol", ctypes.c_double), ("max_refine", ctypes.c_int),
                 ("spin_limit", ctypes.c_int64), ("restart", ctypes.c_int), ("timing", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("precond", ctypes.c_int), ("reserved0", ctypes.c_int), ("mg_omega", ctypes.c_double),
+                ("mg_over", ctypes.c_double), ("reserved", ctypes.c_int * 2)]
 
 
 class StepInfo(ctypes.Structure):

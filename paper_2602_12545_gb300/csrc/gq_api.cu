@@ -166,6 +166,47 @@ void layout(gq_fld_plan* P, Bump& b) {
     w.p32[0] = b.take<float>(N);
     w.p32[1] = b.take<float>(N);
     w.q32 = b.take<float>(N);
+    // multigrid hierarchy: level l has ceil(nx / 2^l) x ceil(ny / 2^l) cells; coarsen until
+    // the level has at most kCoarseMax cells
+    {
+        auto& mg = w.mg;
+        int lx = P->nx, ly = P->ny, nl = 0;
+        while (true) {
+            gq::MGLevel& L = mg.L[nl];
+            L.nx = lx;
+            L.ny = ly;
+            L.N = lx * ly;
+            const size_t n = (size_t)L.N;
+            if (nl == 0) {
+                L.m = L.wW = L.wS = L.s = nullptr;        // level 0 lives in the workspace
+                L.cW = w.cW32;
+                L.cS = w.cS32;
+            } else {
+                L.m = b.take<double>(n);
+                L.wW = b.take<double>(n);
+                L.wS = b.take<double>(n);
+                L.s = b.take<double>(n);
+                L.cW = b.take<float>(n);
+                L.cS = b.take<float>(n);
+            }
+            L.t = b.take<float>(n);
+            L.xa = b.take<float>(n);
+            L.xb = b.take<float>(n);
+            L.r = nl == 0 ? nullptr : b.take<float>(n);
+            nl++;
+            if (L.N <= gq::kCoarseMax || nl == gq::kMaxLevels || (lx == 1 && ly == 1)) break;
+            lx = (lx + 1) / 2;
+            ly = (ly + 1) / 2;
+        }
+        mg.nlev = nl;
+        const int nc = mg.L[nl - 1].N;
+        mg.dense = b.take<double>((size_t)nc * 2 * nc);
+        mg.inv = b.take<float>((size_t)nc * nc);
+        mg.z = b.take<float>(N);
+        mg.zold = b.take<float>(N);
+        mg.r32 = b.take<float>(N);
+        mg.p64s = nullptr;
+    }
     w.partials = b.take<double>(2 * (size_t)P->solve_grid_max * gq::kSlots);
     w.epart = b.take<double>(2 * (size_t)P->setup_blocks);
     w.bar = b.take<unsigned>(2);
@@ -222,6 +263,10 @@ gq_status make_step_params(const gq_fld_plan* P, const double* rho, double* e_g,
     if (opts.prec == GQ_PREC_MIXED && (!(opts.inner_rtol > 0.0) || !(opts.inner_rtol < 1.0)))
         return GQ_ERR_INVALID_ARG;
     if (opts.max_refine < 1 || opts.spin_limit < 0) return GQ_ERR_INVALID_ARG;
+    if (opts.precond != GQ_PRECOND_JACOBI && opts.precond != GQ_PRECOND_MG) return GQ_ERR_INVALID_ARG;
+    const double omega = opts.mg_omega == 0.0 ? 0.8 : opts.mg_omega;
+    const double over = opts.mg_over == 0.0 ? 1.5 : opts.mg_over;
+    if (!(omega > 0.0 && omega <= 1.0) || !(over > 0.0 && over < 2.0)) return GQ_ERR_INVALID_ARG;
 
     StepParams sp{};
     sp.nx = P->nx;
@@ -230,6 +275,7 @@ gq_status make_step_params(const gq_fld_plan* P, const double* rho, double* e_g,
     for (int s = 0; s < 4; s++) sp.bc[s] = bc->side[s];
     sp.limiter = opts.limiter;
     sp.mixed = opts.prec == GQ_PREC_MIXED;
+    sp.precond = opts.precond;
     for (int t = 0; t < 4; t++) {
         sp.kR[t] = kR[t];
         sp.kP[t] = kP[t];
@@ -252,6 +298,9 @@ gq_status make_step_params(const gq_fld_plan* P, const double* rho, double* e_g,
     pp.rtol = opts.rtol;
     pp.drop = opts.inner_rtol;
     pp.spin_limit = opts.spin_limit > 0 ? opts.spin_limit : kDefaultSpin;
+    pp.precond = opts.precond;
+    pp.mg_omega = (float)omega;
+    pp.mg_over = (float)over;
     *sp_out = sp;
     *pp_out = pp;
     if (timing) *timing = opts.timing;
@@ -306,6 +355,10 @@ void gq_solver_opts_default(gq_solver_opts* o) {
     o->max_refine = 200;
     o->spin_limit = 0;
     o->restart = 0;
+    o->timing = 0;
+    o->precond = GQ_PRECOND_MG;
+    o->mg_omega = 0.8;
+    o->mg_over = 1.5;
 }
 
 gq_status gq_fld_setup(const gq_grid_desc* gd, gq_fld_plan** out) {

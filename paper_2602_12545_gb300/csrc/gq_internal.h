@@ -35,6 +35,36 @@ struct DeviceGeometry {
     const double *V, *gx, *gy, *dxf, *thx, *ymet, *dyf, *thy;
 };
 
+// Aggregation multigrid hierarchy (preconditioner of the Krylov solve).  Level 0 is the
+// Jacobi-scaled fine system itself; level l+1 aggregates 2 x 2 cells of level l.  Every
+// level is stored Jacobi-scaled (unit diagonal): c_W, c_S are its scaled couplings and
+// t[k] = s_{l+1}[parent(k)] / s_l[k] the transfer weight of cell k to its parent, so that
+// restriction is r_{l+1}[I] = sum_{k in I} t[k] r_l[k] and prolongation its transpose.
+// The FP64 arrays hold the unscaled Galerkin operator (mass m and face weights) from
+// which the next level is built.
+constexpr int kMaxLevels = 32;
+constexpr int kCoarseMax = 32;       // the coarsest level is solved densely (<= 32 cells)
+constexpr int kBlockLevelMax = 8192; // levels at most this large run inside one block
+
+struct MGLevel {
+    int nx, ny, N;
+    double *m, *wW, *wS, *s;    // unscaled Galerkin operator and diag^{-1/2} (levels >= 1)
+    float *cW, *cS;             // scaled couplings (level 0: the workspace's FP32 copies)
+    float *t;                   // transfer weight to the parent (all but the coarsest level)
+    float *xa, *xb, *r;         // smoother buffers and right-hand side (level 0: r is the CG residual)
+};
+
+struct MGHierarchy {
+    int nlev;                   // levels including level 0 (1 = no coarse levels)
+    MGLevel L[kMaxLevels];
+    double* dense;              // FP64 scratch for the coarsest inverse [nc][2 nc]
+    float* inv;                 // inverse of the coarsest scaled operator [nc][nc]
+    float* z;                   // FP32 preconditioned residual of level 0 (two buffers)
+    float* zold;
+    float* r32;                 // FP32 residual for the V-cycle of the FP64 path
+    double* p64s;               // FP64 path: second direction buffer unused (reserved)
+};
+
 // Workspace of one step in device memory.
 struct Workspace {
     // setup outputs (FP64); the scaled system overwrites some in place
@@ -49,18 +79,20 @@ struct Workspace {
     // solve (FP32 inner path)
     float *cW32, *cS32, *d32, *r32, *p32[2], *q32;
     // reductions, barrier, control
+    MGHierarchy mg;
     double *partials;    // [2][max_blocks][kSlots]
     double *epart;       // [2][max_setup_blocks] energy partial sums (before, after)
     unsigned *bar;       // [2]
     SolveCtl *ctl;
 };
 
-constexpr int kSlots = 5;
+constexpr int kSlots = 6;
 constexpr int kSolveThreads = 512;
 constexpr int kSetupThreads = 256;
 
 struct StepParams {
     int nx, ny, N;
+    int precond;
     int bc[4];
     int limiter;
     int mixed;
@@ -80,6 +112,10 @@ struct SolveParams {
     int max_iter, max_refine;
     double rtol, drop;
     long long spin_limit;
+    int precond;         // GQ_PRECOND_JACOBI or GQ_PRECOND_MG
+    float mg_omega;      // Jacobi smoothing weight of the V-cycle
+    float mg_over;       // coarse-correction over-relaxation
+    int pad;
 };
 
 // status of a problem of a batch that no team has solved yet

@@ -98,6 +98,31 @@ __device__ __forceinline__ void st64(double* p, const double (&o)[W]) {
     }
 }
 
+// W floats (W = 1, 2 or 4) at an address aligned to 4 W bytes
+template <int W>
+__device__ __forceinline__ void ldf(const float* p, float (&o)[W]) {
+    if constexpr (W == 1) {
+        o[0] = __ldcg(p);
+    } else if constexpr (W == 2) {
+        const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+        o[0] = v.x; o[1] = v.y;
+    } else {
+        const float4 v = __ldcg(reinterpret_cast<const float4*>(p));
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void stf(float* p, const float (&o)[W]) {
+    if constexpr (W == 1) {
+        p[0] = o[0];
+    } else if constexpr (W == 2) {
+        *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
+    } else {
+        *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+}
+
 // Block-reduce NSUM sums and NMAX maxima, publish the block partials, wait for all
 // blocks of the team, reduce the partials (same order in every block).  Returns false
 // on timeout.
@@ -154,10 +179,20 @@ __device__ __forceinline__ bool allreduce(double (&v)[NSUM + NMAX], double* part
     return true;
 }
 
-// Solve of one problem by one team of co-resident blocks, W cells per thread and pass.
+}  // namespace
+}  // namespace gq
+
+#include "gq_mg.cuh"
+
+namespace gq {
+namespace {
+
+// Solve of one problem by one team of co-resident blocks, W cells per thread and pass;
+// MG selects the multigrid preconditioner (otherwise Jacobi, i.e. plain CG on A^).
 // Returns false when a wait of the team timed out (the caller must leave the kernel).
-template <bool MIXED, int W>
-__device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspace& w, Team team, RedShared& sh) {
+template <bool MIXED, int W, bool MG>
+__device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspace& w, Team team, RedShared& sh,
+                                            MGShared& msh) {
     using R = std::conditional_t<MIXED, float, double>;
     const int N = P.N, nx = P.nx;
     const int nchunk = N / W;          // N is a multiple of W because nx is
@@ -189,6 +224,17 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
     if (flags) {
         if (tid == 0) ctl->status = (flags & 2) ? kErrNonfinite : kErrInvalid;
         return true;
+    }
+    // multigrid: the rest of the hierarchy, the FP32 level-0 right-hand side and the two
+    // preconditioned-residual buffers
+    float* r0 = MIXED ? w.r32 : w.mg.r32;
+    float* zc = w.mg.z;
+    float* zo = w.mg.zold;
+    if constexpr (MG) {
+        if (!mg_build(w, team, tid, stride, P.spin_limit, abort_flag, msh)) {
+            if (threadIdx.x == 0) atomicExch(&ctl->status, kErrTimeout);
+            return false;
+        }
     }
 
     // ---- FP64 residual r64 = b^ - A^ y and its norms ----------------------------------
@@ -254,8 +300,11 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
     if (crit <= P.rtol) { status = kOk; goto done; }
 
     {
-        // power-of-two scale for the FP32 residual (1 for the FP64 path)
-        const double scale = MIXED ? exp2(-(double)ilogb(tr[4] > 0.0 ? tr[4] : 1.0)) : 1.0;
+        // power-of-two scale that keeps FP32 residual entries O(1): the Krylov residual of
+        // the mixed path and the V-cycle input of both paths carry it (the FP64 Krylov
+        // vectors of the FP64 path do not)
+        const double zs = exp2(-(double)ilogb(tr[4] > 0.0 ? tr[4] : 1.0));
+        const double scale = MIXED ? zs : 1.0;
         double rr = tr[0] * scale * scale;
         double rr_ref = rr;
         double beta = 0.0;
@@ -267,139 +316,35 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
         double rec_target = P.rtol;
         double best = crit;
         int stall = 0;
-
-        while (true) {
-            // ---- S: p = r + beta p_old ; q = A^ p ; p.q ------------------------------
-            const R* __restrict__ pold = pb[cur];
-            R* __restrict__ pnew = pb[cur ^ 1];
-            const R rb = static_cast<R>(beta);
-            const R rsc = static_cast<R>(scale);
-            double v1[1] = {0.0};
+        // multigrid: FP32 copy of the (scaled) FP64 residual for the V-cycle
+        bool first = true;
+        double rz_prev = 1.0;
+        const R rzf = static_cast<R>(MIXED ? 1.0 : 1.0 / zs);
+        auto refresh = [&](bool initial) -> bool {
             for (int c = tid; c < nchunk; c += stride) {
                 const int k = c * W;
-                const bool hs = k >= nx, hn = k + nx < N, hw = k > 0, he = k + W < N;
-                // r on the cells and their west, east, south and north neighbours
-                R rc[W], rs[W], rn[W], rw = R(0), re = R(0);
-                R pc[W], ps[W], pn[W], pw = R(0), pe = R(0);
-#pragma unroll
-                for (int i = 0; i < W; i++) rs[i] = rn[i] = pc[i] = ps[i] = pn[i] = R(0);
-                if (MIXED && from64) {
-                    double t[W];
-                    ld64<W>(r64 + k, t);
-#pragma unroll
-                    for (int i = 0; i < W; i++) rc[i] = static_cast<R>(t[i]) * rsc;
-                    if (hs) {
-                        ld64<W>(r64 + k - nx, t);
-#pragma unroll
-                        for (int i = 0; i < W; i++) rs[i] = static_cast<R>(t[i]) * rsc;
-                    }
-                    if (hn) {
-                        ld64<W>(r64 + k + nx, t);
-#pragma unroll
-                        for (int i = 0; i < W; i++) rn[i] = static_cast<R>(t[i]) * rsc;
-                    }
-                    if (hw) rw = static_cast<R>(__ldcg(r64 + k - 1)) * rsc;
-                    if (he) re = static_cast<R>(__ldcg(r64 + k + W)) * rsc;
-                } else {
-                    ldv<R, W>(r + k, rc);
-                    if (hs) ldv<R, W>(r + k - nx, rs);
-                    if (hn) ldv<R, W>(r + k + nx, rn);
-                    if (hw) rw = __ldcg(r + k - 1);
-                    if (he) re = __ldcg(r + k + W);
-                }
-                if (use_p) {
-                    ldv<R, W>(pold + k, pc);
-                    if (hs) ldv<R, W>(pold + k - nx, ps);
-                    if (hn) ldv<R, W>(pold + k + nx, pn);
-                    if (hw) pw = __ldcg(pold + k - 1);
-                    if (he) pe = __ldcg(pold + k + W);
-                }
-                R cw[W], cs[W], csn[W], cwe = R(0);
-#pragma unroll
-                for (int i = 0; i < W; i++) csn[i] = R(0);
-                ldv<R, W>(cW + k, cw);
-                ldv<R, W>(cS + k, cs);
-                if (he) cwe = cW[k + W];
-                if (hn) ldv<R, W>(cS + k + nx, csn);
-                // p = r + beta p_old on the cells and their neighbours (zero off the grid)
-                R p[W], pS[W], pN[W];
-                const R pW = use_p ? rw + rb * pw : rw;
-                const R pE = use_p ? re + rb * pe : re;
+                double t[W];
+                float f[W], zero[W];
+                ld64<W>(r64 + k, t);
 #pragma unroll
                 for (int i = 0; i < W; i++) {
-                    p[i] = use_p ? rc[i] + rb * pc[i] : rc[i];
-                    pS[i] = use_p ? rs[i] + rb * ps[i] : rs[i];
-                    pN[i] = use_p ? rn[i] + rb * pn[i] : rn[i];
+                    f[i] = static_cast<float>(t[i] * zs);
+                    zero[i] = 0.f;
                 }
-                R qv[W];
-#pragma unroll
-                for (int i = 0; i < W; i++) {
-                    const R left = i == 0 ? pW : p[i - 1];
-                    const R right = i == W - 1 ? pE : p[i + 1];
-                    const R cright = i == W - 1 ? cwe : cw[i + 1];
-                    qv[i] = p[i] - cw[i] * left - cright * right - cs[i] * pS[i] - csn[i] * pN[i];
-                    v1[0] += static_cast<double>(p[i]) * static_cast<double>(qv[i]);
-                }
-                stv<R, W>(pnew + k, p);
-                stv<R, W>(q + k, qv);
-                if (MIXED && from64) {
-                    R zero[W];
-#pragma unroll
-                    for (int i = 0; i < W; i++) zero[i] = R(0);
-                    stv<R, W>(r + k, rc);
-                    stv<R, W>(d + k, zero);
-                }
+                stf<W>(r0 + k, f);
+                if constexpr (MIXED) stf<W>(reinterpret_cast<float*>(d) + k, zero);
+                if (initial) stf<W>(zo + k, zero);
             }
-            if (!allreduce<1, 0>(v1, w.partials, parity, w.bar, P.spin_limit, abort_flag, sh, team)) {
-                timed_out = true;
-                break;
-            }
-            const double pq = v1[0];
-            if (!(pq > 0.0) || !isfinite(pq)) { status = kErrNonfinite; break; }
-            const double alpha = rr / pq;
-            cur ^= 1;
+            return team_barrier(w.bar, team, P.spin_limit, abort_flag);
+        };
+        if constexpr (MG) {
             from64 = false;
+            if (!refresh(true)) { timed_out = true; goto done; }
+        }
 
-            // ---- U: x += alpha p ; r -= alpha q ; r.r --------------------------------
-            double v2[2] = {0.0, 0.0};
-            const R ra = static_cast<R>(alpha);
-            for (int c = tid; c < nchunk; c += stride) {
-                const int k = c * W;
-                R pk[W], qk[W], rk[W], xk[W];
-                ldv<R, W>(pnew + k, pk);
-                ldv<R, W>(q + k, qk);
-                ldv<R, W>(r + k, rk);
-                ldv<R, W>(d + k, xk);
-#pragma unroll
-                for (int i = 0; i < W; i++) {
-                    rk[i] = rk[i] - ra * qk[i];
-                    xk[i] = xk[i] + ra * pk[i];
-                    v2[0] += static_cast<double>(rk[i]) * static_cast<double>(rk[i]);
-                    // recursive stop estimate in FP32 (FP64 division is slow on this part;
-                    // the decisive test uses the exact FP64 residual)
-                    if constexpr (!MIXED)
-                        v2[1] = nanmax(v2[1], (double)__fdividef((float)fabs(rk[i]), (float)fabs(xk[i])));
-                }
-                stv<R, W>(r + k, rk);
-                stv<R, W>(d + k, xk);
-            }
-            if (!allreduce<1, 1>(v2, w.partials, parity, w.bar, P.spin_limit, abort_flag, sh, team)) {
-                timed_out = true;
-                break;
-            }
-            it++;
-            const double rr_new = v2[0];
-            if (!isfinite(rr_new)) { status = kErrNonfinite; break; }
-            const bool check = MIXED ? (sqrt(rr_new) <= P.drop * sqrt(rr_ref) || it >= P.max_iter)
-                                     : (v2[1] <= rec_target || it >= P.max_iter);
-            if (!check) {
-                beta = rr_new / rr;
-                rr = rr_new;
-                use_p = true;
-                continue;
-            }
-
-            // ---- FP64 residual (refinement) -----------------------------------------
+        // FP64 residual (refinement): fold the FP32 correction into y (mixed), recompute
+        // b^ - A^ y, apply the stop tests; false ends the solve (status or timed_out set)
+        auto refine = [&]() -> bool {
             if constexpr (MIXED) {
                 const double inv = 1.0 / scale;
                 for (int c = tid; c < nchunk; c += stride) {
@@ -416,14 +361,20 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
                     st64<W>(y + k, yk);
                     stv<R, W>(d + k, zero);
                 }
-                if (!team_barrier(w.bar, team, P.spin_limit, abort_flag)) { timed_out = true; break; }
+                if (!team_barrier(w.bar, team, P.spin_limit, abort_flag)) {
+                    timed_out = true;
+                    return false;
+                }
             }
-            if (!true_residual(false)) { timed_out = true; break; }
+            if (!true_residual(false)) {
+                timed_out = true;
+                return false;
+            }
             nref++;
             crit = tr[3];
             l2 = sqrt(tr[1] / bb);
-            if (!isfinite(tr[0]) || !(crit == crit)) { status = kErrNonfinite; break; }
-            if (crit <= P.rtol) { status = kOk; break; }
+            if (!isfinite(tr[0]) || !(crit == crit)) { status = kErrNonfinite; return false; }
+            if (crit <= P.rtol) { status = kOk; return false; }
             if (crit < kStallGain * best) {
                 best = crit;
                 stall = 0;
@@ -432,20 +383,226 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
             }
             if (it >= P.max_iter || nref >= P.max_refine || stall >= kStallChecks) {
                 status = kErrNotConverged;
-                break;
+                return false;
             }
             rec_target *= 0.5;
             const double rr_true = tr[0] * scale * scale;
             if (MIXED && P.restart) {
                 use_p = false;
                 beta = 0.0;
+                first = true;
             } else {
                 use_p = true;
-                beta = rr_true / rr;
+                beta = rr > 0.0 ? rr_true / rr : 0.0;
             }
             rr = rr_true;
             rr_ref = rr_true;
-            from64 = MIXED;
+            from64 = MIXED && !MG;
+            if constexpr (MG) {
+                if (!refresh(false)) {
+                    timed_out = true;
+                    return false;
+                }
+            }
+            return true;
+        };
+
+        while (true) {
+            double rho_mg = 0.0;
+            bool degenerate = false;
+            if constexpr (MG) {
+                // ---- z = V-cycle(r) ; r.z and r.z_old (Polak-Ribiere) ---------------------
+                double vz[2] = {0.0, 0.0};
+                if (!vcycle(w.mg, r0, zc, zo, P.mg_omega, P.mg_over, team, tid, stride, w.bar, P.spin_limit,
+                            abort_flag, &vz[0], &vz[1])) {
+                    timed_out = true;
+                    break;
+                }
+                if (!allreduce<2, 0>(vz, w.partials, parity, w.bar, P.spin_limit, abort_flag, sh, team)) {
+                    timed_out = true;
+                    break;
+                }
+                if (!isfinite(vz[0]) || !isfinite(vz[1])) { status = kErrNonfinite; break; }
+                // a vanished recursive residual (FP32) goes straight to the FP64 check
+                degenerate = !(vz[0] > 0.0);
+                // Polak-Ribiere beta, restarted (beta = 0) when the new preconditioned
+                // residual is far from orthogonal to the old one (Powell's test): near
+                // convergence z is rounding noise and the formula could cancel it
+                const bool restart_dir = first || fabs(vz[1]) >= 0.2 * vz[0];
+                beta = restart_dir ? 0.0 : fmax(0.0, (vz[0] - vz[1]) / rz_prev);
+                use_p = !restart_dir;
+                rz_prev = vz[0];
+                rho_mg = vz[0] * static_cast<double>(rzf) * static_cast<double>(rzf);
+                first = false;
+            }
+            if (!degenerate) {
+                // ---- S: p = r + beta p_old ; q = A^ p ; p.q ------------------------------
+                const R* __restrict__ pold = pb[cur];
+                R* __restrict__ pnew = pb[cur ^ 1];
+                const R rb = static_cast<R>(beta);
+                const R rsc = static_cast<R>(scale);
+                double v1[1] = {0.0};
+                for (int c = tid; c < nchunk; c += stride) {
+                    const int k = c * W;
+                    const bool hs = k >= nx, hn = k + nx < N, hw = k > 0, he = k + W < N;
+                    // r on the cells and their west, east, south and north neighbours
+                    R rc[W], rs[W], rn[W], rw = R(0), re = R(0);
+                    R pc[W], ps[W], pn[W], pw = R(0), pe = R(0);
+    #pragma unroll
+                    for (int i = 0; i < W; i++) rs[i] = rn[i] = pc[i] = ps[i] = pn[i] = R(0);
+                    if constexpr (MG) {
+                        float t[W];
+                        ldf<W>(zc + k, t);
+    #pragma unroll
+                        for (int i = 0; i < W; i++) rc[i] = static_cast<R>(t[i]) * rzf;
+                        if (hs) {
+                            ldf<W>(zc + k - nx, t);
+    #pragma unroll
+                            for (int i = 0; i < W; i++) rs[i] = static_cast<R>(t[i]) * rzf;
+                        }
+                        if (hn) {
+                            ldf<W>(zc + k + nx, t);
+    #pragma unroll
+                            for (int i = 0; i < W; i++) rn[i] = static_cast<R>(t[i]) * rzf;
+                        }
+                        if (hw) rw = static_cast<R>(__ldcg(zc + k - 1)) * rzf;
+                        if (he) re = static_cast<R>(__ldcg(zc + k + W)) * rzf;
+                    } else if (MIXED && from64) {
+                        double t[W];
+                        ld64<W>(r64 + k, t);
+    #pragma unroll
+                        for (int i = 0; i < W; i++) rc[i] = static_cast<R>(t[i]) * rsc;
+                        if (hs) {
+                            ld64<W>(r64 + k - nx, t);
+    #pragma unroll
+                            for (int i = 0; i < W; i++) rs[i] = static_cast<R>(t[i]) * rsc;
+                        }
+                        if (hn) {
+                            ld64<W>(r64 + k + nx, t);
+    #pragma unroll
+                            for (int i = 0; i < W; i++) rn[i] = static_cast<R>(t[i]) * rsc;
+                        }
+                        if (hw) rw = static_cast<R>(__ldcg(r64 + k - 1)) * rsc;
+                        if (he) re = static_cast<R>(__ldcg(r64 + k + W)) * rsc;
+                    } else {
+                        ldv<R, W>(r + k, rc);
+                        if (hs) ldv<R, W>(r + k - nx, rs);
+                        if (hn) ldv<R, W>(r + k + nx, rn);
+                        if (hw) rw = __ldcg(r + k - 1);
+                        if (he) re = __ldcg(r + k + W);
+                    }
+                    if (use_p) {
+                        ldv<R, W>(pold + k, pc);
+                        if (hs) ldv<R, W>(pold + k - nx, ps);
+                        if (hn) ldv<R, W>(pold + k + nx, pn);
+                        if (hw) pw = __ldcg(pold + k - 1);
+                        if (he) pe = __ldcg(pold + k + W);
+                    }
+                    R cw[W], cs[W], csn[W], cwe = R(0);
+    #pragma unroll
+                    for (int i = 0; i < W; i++) csn[i] = R(0);
+                    ldv<R, W>(cW + k, cw);
+                    ldv<R, W>(cS + k, cs);
+                    if (he) cwe = cW[k + W];
+                    if (hn) ldv<R, W>(cS + k + nx, csn);
+                    // p = r + beta p_old on the cells and their neighbours (zero off the grid)
+                    R p[W], pS[W], pN[W];
+                    const R pW = use_p ? rw + rb * pw : rw;
+                    const R pE = use_p ? re + rb * pe : re;
+    #pragma unroll
+                    for (int i = 0; i < W; i++) {
+                        p[i] = use_p ? rc[i] + rb * pc[i] : rc[i];
+                        pS[i] = use_p ? rs[i] + rb * ps[i] : rs[i];
+                        pN[i] = use_p ? rn[i] + rb * pn[i] : rn[i];
+                    }
+                    R qv[W];
+    #pragma unroll
+                    for (int i = 0; i < W; i++) {
+                        const R left = i == 0 ? pW : p[i - 1];
+                        const R right = i == W - 1 ? pE : p[i + 1];
+                        const R cright = i == W - 1 ? cwe : cw[i + 1];
+                        qv[i] = p[i] - cw[i] * left - cright * right - cs[i] * pS[i] - csn[i] * pN[i];
+                        v1[0] += static_cast<double>(p[i]) * static_cast<double>(qv[i]);
+                    }
+                    stv<R, W>(pnew + k, p);
+                    stv<R, W>(q + k, qv);
+                    if (MIXED && from64) {
+                        R zero[W];
+    #pragma unroll
+                        for (int i = 0; i < W; i++) zero[i] = R(0);
+                        stv<R, W>(r + k, rc);
+                        stv<R, W>(d + k, zero);
+                    }
+                }
+                if (!allreduce<1, 0>(v1, w.partials, parity, w.bar, P.spin_limit, abort_flag, sh, team)) {
+                    timed_out = true;
+                    break;
+                }
+                const double pq = v1[0];
+                if (!isfinite(pq) || (!MG && !(pq > 0.0))) { status = kErrNonfinite; break; }
+                // multigrid: a degenerate direction (rounding noise at convergence) goes to the
+                // FP64 check
+                degenerate = !(pq > 0.0);
+                if (!degenerate) {
+                    const double alpha = (MG ? rho_mg : rr) / pq;
+                    if constexpr (MG) {
+                        float* tz = zc;       // this z becomes z_old of the next cycle
+                        zc = zo;
+                        zo = tz;
+                    }
+                    cur ^= 1;
+                    from64 = false;
+
+                    // ---- U: x += alpha p ; r -= alpha q ; r.r --------------------------------
+                    double v2[2] = {0.0, 0.0};
+                    const R ra = static_cast<R>(alpha);
+                    for (int c = tid; c < nchunk; c += stride) {
+                        const int k = c * W;
+                        R pk[W], qk[W], rk[W], xk[W];
+                        ldv<R, W>(pnew + k, pk);
+                        ldv<R, W>(q + k, qk);
+                        ldv<R, W>(r + k, rk);
+                        ldv<R, W>(d + k, xk);
+        #pragma unroll
+                        for (int i = 0; i < W; i++) {
+                            rk[i] = rk[i] - ra * qk[i];
+                            xk[i] = xk[i] + ra * pk[i];
+                            v2[0] += static_cast<double>(rk[i]) * static_cast<double>(rk[i]);
+                            // recursive stop estimate in FP32 (FP64 division is slow on this part;
+                            // the decisive test uses the exact FP64 residual)
+                            if constexpr (!MIXED)
+                                v2[1] = nanmax(v2[1], (double)__fdividef((float)fabs(rk[i]), (float)fabs(xk[i])));
+                        }
+                        stv<R, W>(r + k, rk);
+                        stv<R, W>(d + k, xk);
+                        if constexpr (MG && !MIXED) {
+                            float f[W];
+        #pragma unroll
+                            for (int i = 0; i < W; i++) f[i] = static_cast<float>(rk[i] * zs);
+                            stf<W>(r0 + k, f);
+                        }
+                    }
+                    if (!allreduce<1, 1>(v2, w.partials, parity, w.bar, P.spin_limit, abort_flag, sh, team)) {
+                        timed_out = true;
+                        break;
+                    }
+                    it++;
+                    const double rr_new = v2[0];
+                    if (!isfinite(rr_new)) { status = kErrNonfinite; break; }
+                    const bool check = MIXED ? (sqrt(rr_new) <= P.drop * sqrt(rr_ref) || it >= P.max_iter)
+                                             : (v2[1] <= rec_target || it >= P.max_iter);
+                    if (!check) {
+                        if constexpr (!MG) {
+                            beta = rr_new / rr;
+                            use_p = true;
+                        }
+                        rr = rr_new;
+                        continue;
+                    }
+                }
+            }
+
+            if (!refine()) break;
         }
     }
 
@@ -465,31 +622,40 @@ done:
 }
 
 template <bool MIXED>
-__device__ __forceinline__ bool pcg_solve(const SolveParams& P, const Workspace& w, Team team, RedShared& sh) {
+__device__ __forceinline__ bool pcg_solve(const SolveParams& P, const Workspace& w, Team team, RedShared& sh,
+                                          MGShared& msh) {
     constexpr int WV = MIXED ? 4 : 2;
-    if (P.nx % WV == 0) return pcg_solve_w<MIXED, WV>(P, w, team, sh);
-    return pcg_solve_w<MIXED, 1>(P, w, team, sh);
+    const bool vec = P.nx % WV == 0;
+    if (P.precond == GQ_PRECOND_MG)
+        return vec ? pcg_solve_w<MIXED, WV, true>(P, w, team, sh, msh) : pcg_solve_w<MIXED, 1, true>(P, w, team, sh, msh);
+    return vec ? pcg_solve_w<MIXED, WV, false>(P, w, team, sh, msh) : pcg_solve_w<MIXED, 1, false>(P, w, team, sh, msh);
 }
 
-// out-of-line copies for the batched kernel, which holds all four variants: separate
+// out-of-line copies for the batched kernel, which holds all the variants: separate
 // functions keep each variant's registers to itself
-template <bool MIXED, int W>
-__device__ __noinline__ bool pcg_solve_call(const SolveParams& P, const Workspace& w, Team team, RedShared& sh) {
-    return pcg_solve_w<MIXED, W>(P, w, team, sh);
+template <bool MIXED, int W, bool MG>
+__device__ __noinline__ bool pcg_solve_call(const SolveParams& P, const Workspace& w, Team team, RedShared& sh,
+                                            MGShared& msh) {
+    return pcg_solve_w<MIXED, W, MG>(P, w, team, sh, msh);
 }
 
 template <bool MIXED>
 __device__ __forceinline__ bool pcg_solve_outlined(const SolveParams& P, const Workspace& w, Team team,
-                                                   RedShared& sh) {
+                                                   RedShared& sh, MGShared& msh) {
     constexpr int WV = MIXED ? 4 : 2;
-    if (P.nx % WV == 0) return pcg_solve_call<MIXED, WV>(P, w, team, sh);
-    return pcg_solve_call<MIXED, 1>(P, w, team, sh);
+    const bool vec = P.nx % WV == 0;
+    if (P.precond == GQ_PRECOND_MG)
+        return vec ? pcg_solve_call<MIXED, WV, true>(P, w, team, sh, msh)
+                   : pcg_solve_call<MIXED, 1, true>(P, w, team, sh, msh);
+    return vec ? pcg_solve_call<MIXED, WV, false>(P, w, team, sh, msh)
+               : pcg_solve_call<MIXED, 1, false>(P, w, team, sh, msh);
 }
 
 template <bool MIXED>
 __global__ void __launch_bounds__(kSolveThreads, 1) k_pcg(SolveParams P, Workspace w) {
     __shared__ RedShared sh;
-    pcg_solve<MIXED>(P, w, Team{static_cast<int>(blockIdx.x), static_cast<int>(gridDim.x)}, sh);
+    __shared__ MGShared msh;
+    pcg_solve<MIXED>(P, w, Team{static_cast<int>(blockIdx.x), static_cast<int>(gridDim.x)}, sh, msh);
 }
 
 // Batched persistent solve: the co-resident grid is split into teams; the leader block
@@ -498,6 +664,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_pcg(SolveParams P, Workspa
 // themselves, so small problems (one-block teams) never touch an inter-block barrier.
 __global__ void __launch_bounds__(kSolveThreads, 1) kb_pcg(BatchArgs a) {
     __shared__ RedShared sh;
+    __shared__ MGShared msh;
     __shared__ int s_idx;
     const int tm = a.block_team[blockIdx.x];
     const Team team{static_cast<int>(blockIdx.x) - a.team_first[tm], a.team_size[tm]};
@@ -513,8 +680,8 @@ __global__ void __launch_bounds__(kSolveThreads, 1) kb_pcg(BatchArgs a) {
         const int idx = s_idx;
         if (idx >= qlen) return;
         const ProbDesc& d = a.desc[a.queue[a.class_start[c] + idx]];
-        const bool ok = d.sp.mixed ? pcg_solve_outlined<true>(d.solve, d.w, team, sh)
-                                   : pcg_solve_outlined<false>(d.solve, d.w, team, sh);
+        const bool ok = d.sp.mixed ? pcg_solve_outlined<true>(d.solve, d.w, team, sh, msh)
+                                   : pcg_solve_outlined<false>(d.solve, d.w, team, sh, msh);
         if (!ok) return;
     }
 }

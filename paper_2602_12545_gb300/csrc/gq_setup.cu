@@ -18,8 +18,26 @@ namespace gq {
 
 namespace {
 
+// x^e for the exponents power laws use: integers and half-integers up to 8 by repeated
+// multiplication (and one square root), anything else through pow.  FP64 pow costs tens
+// of FP64 operations, and FP64 arithmetic is the scarce resource of this part.
+__device__ __forceinline__ double power(double x, double e) {
+    if (e == 1.0) return x;
+    if (e == 0.0) return 1.0;
+    const double ae = fabs(e);
+    const double twice = 2.0 * ae;
+    if (ae <= 8.0 && twice == rint(twice)) {
+        const int n = static_cast<int>(ae);
+        double r = 1.0;
+        for (int i = 0; i < n; i++) r *= x;
+        if (twice != 2.0 * n) r *= sqrt(x);
+        return e < 0.0 ? 1.0 / r : r;
+    }
+    return pow(x, e);
+}
+
 __device__ __forceinline__ double opacity(const double* k, double rho, double T) {
-    return k[1] != 0.0 ? k[0] + k[1] * pow(rho, k[2]) * pow(T, k[3]) : k[0];
+    return k[1] != 0.0 ? k[0] + k[1] * power(rho, k[2]) * power(T, k[3]) : k[0];
 }
 
 template <int NT>
@@ -56,17 +74,20 @@ __device__ void cells_body(const StepParams& sp, const DeviceGeometry& g, const 
         const double cv = rho * sp.cvfac;
         const double T = e / cv;
         const double kR = opacity(sp.kR, rho, T);
-        const double kP = opacity(sp.kP, rho, T);
+        const bool same = sp.kP[0] == sp.kR[0] && sp.kP[1] == sp.kR[1] && sp.kP[2] == sp.kR[2] &&
+                          sp.kP[3] == sp.kR[3];
+        const double kP = same ? kR : opacity(sp.kP, rho, T);
         const double beta = kP * rho * kC * sp.dt;
         const double aT3 = kARad * T * T * T;
         const double aT4 = aT3 * T;
         const double psi6 = cv + 4.0 * beta * aT3;
-        const double f = cv / psi6;
+        const double ipsi = 1.0 / psi6;
+        const double f = cv * ipsi;
         w.sig[k] = kR * rho;
         w.dloc[k] = V * (1.0 + beta * f);
         w.rhs[k] = V * (E + beta * aT4 * f);
-        w.tA[k] = (e + 3.0 * beta * aT4) / psi6;
-        w.tB[k] = beta / psi6;
+        w.tA[k] = (e + 3.0 * beta * aT4) * ipsi;
+        w.tB[k] = beta * ipsi;
         eloc += V * (E + e);
     }
     if (flags) atomicOr(&w.ctl->input_flags, flags);
@@ -123,6 +144,33 @@ __device__ void faces_body(const StepParams& sp, const DeviceGeometry& g, const 
     }
 }
 
+// Galerkin coarsening of level 0 to level 1 (aggregation multigrid): for each 2 x 2
+// aggregate the mass sum(V (1 + beta~) + Milne term) and the summed weights of the fine
+// faces on the aggregate's west and south sides.  Runs before the diagonal pass, while
+// dloc and the face weights are still unscaled.
+__device__ void coarsen0_body(const StepParams& sp, const Workspace& w, int blk, int nblk) {
+    if (sp.precond != GQ_PRECOND_MG || w.mg.nlev < 2) return;
+    const MGLevel& C = w.mg.L[1];
+    const int nx = sp.nx, ny = sp.ny;
+    for (int c = blk * blockDim.x + threadIdx.x; c < C.N; c += nblk * blockDim.x) {
+        const int jc = c / C.nx, ic = c - jc * C.nx;
+        const int i0 = 2 * ic, j0 = 2 * jc;
+        const int i1 = min(i0 + 1, nx - 1), j1 = min(j0 + 1, ny - 1);
+        double m = 0.0, ww = 0.0, ws = 0.0;
+        for (int j = j0; j <= j1; j++) {
+            for (int i = i0; i <= i1; i++) {
+                const int k = j * nx + i;
+                m += w.dloc[k] + w.wB[k];
+            }
+            ww += w.wW[j * nx + i0];
+        }
+        for (int i = i0; i <= i1; i++) ws += w.wS[j0 * nx + i];
+        C.m[c] = m;
+        C.wW[c] = ww;
+        C.wS[c] = ws;
+    }
+}
+
 // K1c: diagonal of the reduced system and its Jacobi scale s = diag^{-1/2} (in place of dloc)
 __device__ void diag_body(const StepParams& sp, const Workspace& w, int blk, int nblk) {
     const int nx = sp.nx, ny = sp.ny;
@@ -148,7 +196,7 @@ __device__ void scale_body(const StepParams& sp, const Workspace& w, int blk, in
         w.wS[k] = cs;
         w.rhs[k] *= sk;
         w.y[k] = sp.E[k] / sk;
-        if (sp.mixed) {
+        if (sp.mixed || sp.precond == GQ_PRECOND_MG) {
             w.cW32[k] = static_cast<float>(cw);
             w.cS32[k] = static_cast<float>(cs);
         }
@@ -207,6 +255,9 @@ __global__ void __launch_bounds__(kSetupThreads) k_faces(StepParams sp, DeviceGe
 __global__ void __launch_bounds__(kSetupThreads) k_diag(StepParams sp, Workspace w) {
     diag_body(sp, w, blockIdx.x, gridDim.x);
 }
+__global__ void __launch_bounds__(kSetupThreads) k_coarsen0(StepParams sp, Workspace w) {
+    coarsen0_body(sp, w, blockIdx.x, gridDim.x);
+}
 __global__ void __launch_bounds__(kSetupThreads) k_scale(StepParams sp, Workspace w) {
     scale_body(sp, w, blockIdx.x, gridDim.x);
 }
@@ -250,6 +301,11 @@ __global__ void __launch_bounds__(kSetupThreads) kb_faces(BatchArgs a) {
     const ProbDesc& d = a.desc[p];
     faces_body(d.sp, d.g, d.w, blockIdx.x - a.setup_prefix[p], d.setup_blocks);
 }
+__global__ void __launch_bounds__(kSetupThreads) kb_coarsen0(BatchArgs a) {
+    const int p = problem_of_block(a.setup_prefix, a.n, blockIdx.x);
+    const ProbDesc& d = a.desc[p];
+    coarsen0_body(d.sp, d.w, blockIdx.x - a.setup_prefix[p], d.setup_blocks);
+}
 __global__ void __launch_bounds__(kSetupThreads) kb_diag(BatchArgs a) {
     const int p = problem_of_block(a.setup_prefix, a.n, blockIdx.x);
     const ProbDesc& d = a.desc[p];
@@ -279,6 +335,7 @@ cudaError_t launch_setup(const StepParams& sp, const DeviceGeometry& g, const Wo
                          cudaStream_t st) {
     k_cells<<<nblk, kSetupThreads, 0, st>>>(sp, g, w);
     k_faces<<<nblk, kSetupThreads, 0, st>>>(sp, g, w);
+    if (sp.precond == GQ_PRECOND_MG && w.mg.nlev > 1) k_coarsen0<<<nblk, kSetupThreads, 0, st>>>(sp, w);
     k_diag<<<nblk, kSetupThreads, 0, st>>>(sp, w);
     k_scale<<<nblk, kSetupThreads, 0, st>>>(sp, w);
     return cudaGetLastError();
@@ -288,6 +345,7 @@ cudaError_t launch_batch_setup(const BatchArgs& a, int total, cudaStream_t st) {
     kb_init<<<(a.n + 127) / 128, 128, 0, st>>>(a);
     kb_cells<<<total, kSetupThreads, 0, st>>>(a);
     kb_faces<<<total, kSetupThreads, 0, st>>>(a);
+    kb_coarsen0<<<total, kSetupThreads, 0, st>>>(a);
     kb_diag<<<total, kSetupThreads, 0, st>>>(a);
     kb_scale<<<total, kSetupThreads, 0, st>>>(a);
     return cudaGetLastError();

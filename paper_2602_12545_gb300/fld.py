@@ -35,6 +35,9 @@ class SolverOptions:
     spin_limit: int = 0
     restart: int = 0
     timing: int = 0
+    precond: int = 1              # 0 Jacobi, 1 aggregation multigrid V-cycle
+    mg_omega: float = 0.0         # 0 = library default
+    mg_over: float = 0.0
 
     def to_c(self) -> N.SolverOpts:
         o = N.SolverOpts()
@@ -42,6 +45,7 @@ class SolverOptions:
         o.prec, o.limiter, o.rtol, o.max_iter = int(self.prec), int(self.limiter), float(self.rtol), int(self.max_iter)
         o.inner_rtol, o.max_refine = float(self.inner_rtol), int(self.max_refine)
         o.spin_limit, o.restart, o.timing = int(self.spin_limit), int(self.restart), int(self.timing)
+        o.precond, o.mg_omega, o.mg_over = int(self.precond), float(self.mg_omega), float(self.mg_over)
         return o
 
 

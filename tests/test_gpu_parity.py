@@ -89,6 +89,27 @@ def test_config0_fp64(fld, orc):
     assert e0 == pytest.approx(ref["energy_before"], rel=1e-13)
 
 
+@pytest.mark.parametrize("prec,rtol,gate", [(W.PREC_FP64, 1e-12, FP64_GATE), (W.PREC_MIXED, 1e-10, MIXED_GATE)])
+def test_config0_jacobi_preconditioner(fld, orc, prec, rtol, gate):
+    """The plain Jacobi-preconditioned path (no multigrid) reaches the same answer."""
+    P = W.config0()
+    ref = orc.step(P, "lu")
+    out = run_gpu(fld, P, prec, rtol, precond=0)
+    assert out["info"]["status"] == 0
+    check_parity(out, ref, gate)
+
+
+def test_multigrid_cuts_iterations(fld):
+    """Multigrid preconditioning needs several times fewer Krylov iterations than Jacobi
+    on a diffusion-dominated spherical grid."""
+    P = W.config2(nr=256, nth=128)
+    a = run_gpu(fld, P, W.PREC_MIXED, 1e-10, precond=0)
+    b = run_gpu(fld, P, W.PREC_MIXED, 1e-10, precond=1)
+    assert a["info"]["status"] == 0 and b["info"]["status"] == 0
+    assert b["info"]["iterations"] * 4 < a["info"]["iterations"], (a["info"], b["info"])
+    assert relerr(b["E_r"], a["E_r"]) < 1e-7
+
+
 def test_config0_mixed(fld, orc):
     P = W.config0()
     ref = orc.step(P, "lu")
