@@ -167,6 +167,28 @@ gq_status gq_fld_step(gq_fld_plan *plan, const double *rho, double *e_g, double 
 /* Release a plan and its device memory (NULL is ignored). */
 void gq_fld_destroy(gq_fld_plan *plan);
 
+/* Allocation-free single step (the paper has no counterpart).  For callers that cannot
+ * allocate device memory: hosts whose device memory is fixed at start-up, plug-ins inside
+ * another application's memory manager, loops that cannot afford the device
+ * synchronisation of cudaMalloc / cudaFree.  The step is gq_fld_step's, but every piece of device scratch (geometry,
+ * workspace, reductions, control) lives in one static array of gq_fld_step_noalloc_max_bytes()
+ * bytes (32 MiB) that each GPU loading the library holds until the process exits; the call
+ * makes no cudaMalloc / cudaFree / allocating call.  The caller passes inputs and outputs:
+ * x_faces (nx+1) and y_faces (ny+1) as DEVICE arrays, the fields as in gq_fld_step (no
+ * explicit areas or volumes).  Grids whose footprint exceeds the array (about 160 000 cells)
+ * return GQ_ERR_INVALID_ARG before any work.  All calls on a device share the array and it
+ * keeps the previous call's contents; the call resets what must start at zero, and calls
+ * that overlap on the GPU (other streams or host threads) race: serialise them.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  info->t_*_ms are not filled. */
+gq_status gq_fld_step_noalloc(int nx, int ny, int coord, const double *x_faces, const double *y_faces,
+                              const double *rho, double *e_g, double *E_r, double *T_g_out,
+                              const gq_opacity_law *opacity, const gq_eos *eos, double dt, const gq_bc *bc,
+                              const gq_solver_opts *opts, void *stream, gq_step_info *info);
+
+/* Size in bytes of the static scratch array behind gq_fld_step_noalloc. */
+size_t gq_fld_step_noalloc_max_bytes(void);
+
 /* ---------------------------------------------------------------------------------------
  * Batched steps: many independent problems (each with its own plan, i.e. its own grid,
  * Cartesian or spherical-polar, and its own dt, opacity law, boundaries and options) in

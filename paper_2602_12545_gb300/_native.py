@@ -113,6 +113,12 @@ SIGNATURES = {
                                    ctypes.c_double, ctypes.POINTER(Bc), ctypes.POINTER(SolverOpts),
                                    ctypes.c_void_p, ctypes.POINTER(StepInfo)]),
     "gq_fld_destroy": (None, [ctypes.c_void_p]),
+    "gq_fld_step_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.POINTER(OpacityLaw), ctypes.POINTER(Eos), ctypes.c_double,
+                                           ctypes.POINTER(Bc), ctypes.POINTER(SolverOpts), ctypes.c_void_p,
+                                           ctypes.POINTER(StepInfo)]),
+    "gq_fld_step_noalloc_max_bytes": (ctypes.c_size_t, []),
     "gq_solver_opts_default": (None, [ctypes.POINTER(SolverOpts)]),
     "gq_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "gq_version": (ctypes.c_char_p, []),

@@ -231,6 +231,16 @@ bool size_plan(gq_fld_plan* P) {
     return true;
 }
 
+}  // namespace
+
+size_t gq::plan_layout(gq_fld_plan* P, char* base) {
+    Bump b{base, 0};
+    layout(P, b);
+    return b.off;
+}
+
+namespace {
+
 bool finite_all(const double* v, int n) {
     for (int i = 0; i < n; i++)
         if (!std::isfinite(v[i])) return false;

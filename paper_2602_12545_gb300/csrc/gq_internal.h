@@ -174,6 +174,10 @@ gq_status make_step_params(const gq_fld_plan* P, const double* rho, double* e_g,
                            const gq_opacity_law* op, const gq_eos* eos, double dt, const gq_bc* bc,
                            const gq_solver_opts* opts, StepParams* sp, SolveParams* pp, int* timing);
 gq_status status_of(const SolveCtl& c);
+// lays out a plan's arrays from base (nullptr: sizing only); returns the bytes used.
+// P->nx, ny, N, solve_grid_max and setup_blocks must be set.  Used by the
+// allocation-free step, which places the plan in its static array.
+size_t plan_layout(gq_fld_plan* P, char* base);
 gq_status batch_create_capacity(int device, int num_sms, int cap, const gq_batch_opts* opts, gq_batch** out);
 gq_status batch_rebind(gq_batch* B, gq_fld_plan* const* plans, int n);
 void fill_info(const SolveCtl& c, gq_status status, gq_step_info* info);
