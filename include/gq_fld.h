@@ -47,7 +47,7 @@ enum { GQ_CARTESIAN = 0, GQ_SPHERICAL_POLAR = 1 };
 enum { GQ_BC_REFLECT = 0, GQ_BC_OUTFLOW_MILNE = 1 };
 enum { GQ_LIMITER_LP = 0, GQ_LIMITER_MINERBO = 1, GQ_LIMITER_NONE = 2 };
 enum { GQ_PREC_FP64 = 0, GQ_PREC_MIXED = 1 };
-enum { GQ_PRECOND_JACOBI = 0, GQ_PRECOND_MG = 1 };
+enum { GQ_PRECOND_JACOBI = 0, GQ_PRECOND_MG = 1, GQ_PRECOND_AMG = 2 };
 
 /* Grid geometry (Sec. 3.2.1 and Eq. fldg).  Cartesian (x, y) per unit depth, or
  * axisymmetric spherical-polar (r, theta) with the common factor 2 pi dropped.
@@ -97,9 +97,15 @@ typedef struct { int side[4]; } gq_bc;
  *               multigrid (2 x 2 Galerkin coarsening of the Jacobi-scaled operator, two
  *               weighted-Jacobi sweeps before and after, exact solve of the coarsest
  *               <= 32 cells), in FP32 for both precisions, with Polak-Ribiere directions.
+ *               GQ_PRECOND_AMG: one V-cycle of classical algebraic multigrid, built on
+ *               the device every step (PMIS coarsening with strength taken on the
+ *               unscaled operator, direct interpolation truncated to 4 entries, Galerkin
+ *               coarse operators), robust where the face weights jump by orders of
+ *               magnitude from cell to cell; FP32 cycle for both precisions.
  *               GQ_PRECOND_JACOBI: diagonal (Jacobi) preconditioning only.
  *   mg_omega    Jacobi smoothing weight of the V-cycle, in (0, 1] (0 = default 0.8).
- *   mg_over     coarse-correction factor, in (0, 2) (0 = default 1.5). */
+ *   mg_over     coarse-correction factor, in (0, 2) (0 = default 1.5; the AMG cycle
+ *               applies no factor). */
 typedef struct {
     int prec;
     int limiter;
@@ -130,7 +136,10 @@ typedef struct {
     double t_setup_ms;          /* with opts.timing: set-up kernels (coefficients, scaling) */
     double t_solve_ms;          /* with opts.timing: the Krylov solve kernel */
     double t_finish_ms;         /* with opts.timing: back-substitution and energy sums */
-    int reserved[4];
+    float t_precond_ms;         /* device clock: build of the preconditioner inside the solve */
+    float t_iter_us;            /* device clock: solve time after that build per Krylov iteration */
+    int precond_levels;         /* levels of the multigrid hierarchy (1 for Jacobi) */
+    int reserved;
 } gq_step_info;
 
 typedef struct gq_fld_plan gq_fld_plan;
@@ -166,6 +175,25 @@ gq_status gq_fld_step(gq_fld_plan *plan, const double *rho, double *e_g, double 
 
 /* Release a plan and its device memory (NULL is ignored). */
 void gq_fld_destroy(gq_fld_plan *plan);
+
+/* Multigrid hierarchy of a plan's last step (diagnostics; the paper's solver builds no
+ * hierarchy).  For GQ_PRECOND_AMG: rows and off-diagonal entries of every level as built
+ * on the device, why coarsening stopped (1 coarsest small enough, 2 level cap, 3 a level
+ * did not shrink, 4 row pool, 5 entry pool, 6 a coarse row too long), and the device time
+ * of each part of the build.  For GQ_PRECOND_MG: the fixed 2 x 2 hierarchy's rows.
+ * Synchronises with the device.  GQ_ERR_INVALID_ARG before any step or for Jacobi. */
+typedef struct {
+    int precond;
+    int levels;
+    int stop_reason;
+    int rows[24];
+    int entries[24];
+    float build_ms[24];         /* AMG: coarsening level l into level l + 1 */
+    float fine_copy_ms;         /* AMG: copy of the fine operator into the hierarchy */
+    float coarsest_ms;          /* AMG: inverse of the coarsest level */
+} gq_precond_info;
+
+gq_status gq_fld_precond_info(const gq_fld_plan *plan, gq_precond_info *out);
 
 /* Allocation-free single step (the paper has no counterpart).  For callers that cannot
  * allocate device memory: hosts whose device memory is fixed at start-up, plug-ins inside

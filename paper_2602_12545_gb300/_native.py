@@ -22,6 +22,7 @@ GQ_ERR_TIMEOUT = 6
 GQ_ERR_BUDGET = 7
 GQ_PRECOND_JACOBI = 0
 GQ_PRECOND_MG = 1
+GQ_PRECOND_AMG = 2
 
 _dp = ctypes.POINTER(ctypes.c_double)
 
@@ -56,10 +57,24 @@ class StepInfo(ctypes.Structure):
                 ("rel_residual_l2", ctypes.c_double), ("energy_before", ctypes.c_double),
                 ("energy_after", ctypes.c_double), ("status", ctypes.c_int), ("solve_blocks", ctypes.c_int),
                 ("t_setup_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double), ("t_finish_ms", ctypes.c_double),
-                ("reserved", ctypes.c_int * 4)]
+                ("t_precond_ms", ctypes.c_float), ("t_iter_us", ctypes.c_float), ("precond_levels", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class PrecondInfo(ctypes.Structure):
+    _fields_ = [("precond", ctypes.c_int), ("levels", ctypes.c_int), ("stop_reason", ctypes.c_int),
+                ("rows", ctypes.c_int * 24), ("entries", ctypes.c_int * 24), ("build_ms", ctypes.c_float * 24),
+                ("fine_copy_ms", ctypes.c_float), ("coarsest_ms", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        n = self.levels
+        return {"precond": self.precond, "levels": n, "stop_reason": self.stop_reason,
+                "rows": list(self.rows[:n]), "entries": list(self.entries[:n]),
+                "build_ms": list(self.build_ms[:max(n - 1, 0)]), "fine_copy_ms": self.fine_copy_ms,
+                "coarsest_ms": self.coarsest_ms}
 
 
 class BatchItem(ctypes.Structure):
@@ -113,6 +128,7 @@ SIGNATURES = {
                                    ctypes.c_double, ctypes.POINTER(Bc), ctypes.POINTER(SolverOpts),
                                    ctypes.c_void_p, ctypes.POINTER(StepInfo)]),
     "gq_fld_destroy": (None, [ctypes.c_void_p]),
+    "gq_fld_precond_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(PrecondInfo)]),
     "gq_fld_step_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.POINTER(OpacityLaw), ctypes.POINTER(Eos), ctypes.c_double,

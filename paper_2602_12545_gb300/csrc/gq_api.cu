@@ -207,6 +207,42 @@ void layout(gq_fld_plan* P, Bump& b) {
         mg.r32 = b.take<float>(N);
         mg.p64s = nullptr;
     }
+    // algebraic multigrid pools: rows of all levels (coarse levels hold at most about half
+    // of their fine level's rows), off-diagonal entries (4 per fine row, about 8 per fine
+    // row over the coarse levels)
+    {
+        auto& a = w.amg;
+        a.n0 = (int)N;
+        a.cap_rows = (int)(2 * N + 64);
+        a.cap_nnz = (int)(12 * N + 1024);
+        const size_t R = (size_t)a.cap_rows, E = (size_t)a.cap_nnz, K = gq::kAmgPmax;
+        a.info = b.take<gq::AMGInfo>(1);
+        a.rowptr = b.take<int>(R + gq::kAmgMaxLevels);
+        a.col = b.take<int>(E);
+        a.a64 = b.take<double>(E);
+        a.a32 = b.take<float>(E);
+        a.sfl = b.take<unsigned char>(E);
+        a.diag = b.take<double>(R);
+        a.s = b.take<double>(R);
+        a.pc = b.take<int>(K * R);
+        a.pv32 = b.take<float>(K * R);
+        a.rrow = b.take<int>(R + gq::kAmgMaxLevels);
+        a.rent = b.take<int>(K * R);
+        a.x = b.take<float>(R);
+        a.b = b.take<float>(R);
+        a.t = b.take<float>(R);
+        a.pv64 = b.take<double>(K * N);
+        a.rowmax = b.take<double>(N);
+        a.wgt = b.take<double>(N);
+        a.stA = b.take<signed char>(N);
+        a.stB = b.take<signed char>(N);
+        a.cidx = b.take<int>(N);
+        a.cf = b.take<int>(N);
+        a.cnt = b.take<int>(N + 1);
+        a.cnt2 = b.take<int>(N + 1);
+        a.dense = b.take<double>((size_t)gq::kCoarseMax * 2 * gq::kCoarseMax);
+        a.inv = b.take<float>((size_t)gq::kCoarseMax * gq::kCoarseMax);
+    }
     w.partials = b.take<double>(2 * (size_t)P->solve_grid_max * gq::kSlots);
     w.epart = b.take<double>(2 * (size_t)P->setup_blocks);
     w.bar = b.take<unsigned>(2);
@@ -273,7 +309,8 @@ gq_status make_step_params(const gq_fld_plan* P, const double* rho, double* e_g,
     if (opts.prec == GQ_PREC_MIXED && (!(opts.inner_rtol > 0.0) || !(opts.inner_rtol < 1.0)))
         return GQ_ERR_INVALID_ARG;
     if (opts.max_refine < 1 || opts.spin_limit < 0) return GQ_ERR_INVALID_ARG;
-    if (opts.precond != GQ_PRECOND_JACOBI && opts.precond != GQ_PRECOND_MG) return GQ_ERR_INVALID_ARG;
+    if (opts.precond != GQ_PRECOND_JACOBI && opts.precond != GQ_PRECOND_MG && opts.precond != GQ_PRECOND_AMG)
+        return GQ_ERR_INVALID_ARG;
     const double omega = opts.mg_omega == 0.0 ? 0.8 : opts.mg_omega;
     const double over = opts.mg_over == 0.0 ? 1.5 : opts.mg_over;
     if (!(omega > 0.0 && omega <= 1.0) || !(over > 0.0 && over < 2.0)) return GQ_ERR_INVALID_ARG;
@@ -332,6 +369,11 @@ void fill_info(const SolveCtl& c, gq_status status, gq_step_info* info) {
     info->energy_before = c.energy0;
     info->energy_after = c.energy1;
     info->status = status;
+    info->t_precond_ms = c.t_built > c.t_start && c.t_start > 0 ? (float)((c.t_built - c.t_start) * 1e-6) : 0.f;
+    info->t_iter_us = c.iterations > 0 && c.t_end > c.t_built && c.t_built > 0
+                          ? (float)((double)(c.t_end - c.t_built) * 1e-3 / c.iterations)
+                          : 0.f;
+    info->precond_levels = c.levels;
 }
 
 }  // namespace gq
@@ -376,13 +418,14 @@ gq_status gq_fld_setup(const gq_grid_desc* gd, gq_fld_plan** out) {
     *out = nullptr;
     if (!gd || !gd->x_faces || !gd->y_faces || gd->nx < 1 || gd->ny < 1) return GQ_ERR_INVALID_ARG;
     if (gd->coord != GQ_CARTESIAN && gd->coord != GQ_SPHERICAL_POLAR) return GQ_ERR_INVALID_ARG;
-    if ((long long)gd->nx * gd->ny > (1ll << 30)) return GQ_ERR_INVALID_ARG;
+    if ((long long)gd->nx * gd->ny > gq::kMaxCells) return GQ_ERR_INVALID_ARG;
     HostGeometry H;
     gq_status st = build_geometry(gd, H);
     if (st != GQ_OK) return st;
 
     gq_fld_plan* P = new (std::nothrow) gq_fld_plan();
     if (!P) return GQ_ERR_OOM;
+    P->last_precond = -1;
     P->nx = gd->nx;
     P->ny = gd->ny;
     P->N = gd->nx * gd->ny;
@@ -435,7 +478,7 @@ gq_status gq_fld_setup(const gq_grid_desc* gd, gq_fld_plan** out) {
 size_t gq_fld_plan_bytes(const gq_fld_plan* P) { return P ? P->arena_bytes : 0; }
 
 size_t gq_fld_plan_bytes_for(int nx, int ny) {
-    if (nx < 1 || ny < 1 || (long long)nx * ny > (1ll << 30)) return 0;
+    if (nx < 1 || ny < 1 || (long long)nx * ny > gq::kMaxCells) return 0;
     gq_fld_plan tmp{};
     tmp.nx = nx;
     tmp.ny = ny;
@@ -450,6 +493,47 @@ void gq_fld_destroy(gq_fld_plan* P) {
     for (int t = 0; t < 4; t++)
         if (P->ev[t]) cudaEventDestroy(P->ev[t]);
     delete P;
+}
+
+gq_status gq_fld_precond_info(const gq_fld_plan* P, gq_precond_info* out) {
+    if (!P || !out) return GQ_ERR_INVALID_ARG;
+    std::memset(out, 0, sizeof(*out));
+    out->precond = P->last_precond;
+    if (P->last_precond == GQ_PRECOND_MG) {
+        const gq::MGHierarchy& mg = P->ws.mg;
+        out->levels = mg.nlev;
+        out->stop_reason = 1;
+        for (int l = 0; l < mg.nlev && l < 24; l++) {
+            const gq::MGLevel& L = mg.L[l];
+            out->rows[l] = L.N;
+            out->entries[l] = 2 * ((L.nx - 1) * L.ny + L.nx * (L.ny - 1));
+        }
+        return GQ_OK;
+    }
+    if (P->last_precond != GQ_PRECOND_AMG) return GQ_ERR_INVALID_ARG;
+    gq::AMGInfo I{};
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return GQ_ERR_CUDA;
+    if (cur != P->device && cudaSetDevice(P->device) != cudaSuccess) return GQ_ERR_CUDA;
+    cudaError_t e = cudaMemcpy(&I, P->ws.amg.info, sizeof(I), cudaMemcpyDeviceToHost);
+    if (cur != P->device) cudaSetDevice(cur);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return GQ_ERR_CUDA;
+    }
+    const int nl = std::min(std::max(I.nlev, 0), std::min(gq::kAmgMaxLevels, 24));
+    out->levels = nl;
+    out->stop_reason = I.stop;
+    for (int l = 0; l < nl; l++) {
+        out->rows[l] = I.n[l];
+        out->entries[l] = I.nnz[l];
+        if (l + 1 < nl) out->build_ms[l] = (float)((I.tns[2 + l] - I.tns[1 + l]) * 1e-6);
+    }
+    if (nl > 0) {
+        out->fine_copy_ms = (float)((I.tns[1] - I.tns[0]) * 1e-6);
+        out->coarsest_ms = (float)((I.tns[nl + 1] - I.tns[nl]) * 1e-6);
+    }
+    return GQ_OK;
 }
 
 gq_status gq_fld_step(gq_fld_plan* P, const double* rho, double* e_g, double* E_r, double* T_g_out,
@@ -471,6 +555,7 @@ gq_status gq_fld_step(gq_fld_plan* P, const double* rho, double* e_g, double* E_
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 
     const bool timing = timing_flag != 0;
+    P->last_precond = pp.precond;
     cudaError_t e = cudaMemsetAsync(P->ws.ctl, 0, sizeof(gq::SolveCtl), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->ws.bar, 0, 2 * sizeof(unsigned), st);
     if (e == cudaSuccess && timing) e = cudaEventRecord(P->ev[0], st);

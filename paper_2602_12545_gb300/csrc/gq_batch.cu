@@ -277,6 +277,7 @@ gq_status fill_descs(gq_batch* B, const gq_batch_item* items) {
         d.solve = pp;
         d.setup_blocks = B->prefix[p + 1] - B->prefix[p];
         d.pad = 0;
+        const_cast<gq_fld_plan*>(P)->last_precond = pp.precond;
     }
     return GQ_OK;
 }

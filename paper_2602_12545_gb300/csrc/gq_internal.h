@@ -21,7 +21,10 @@ struct SolveCtl {
     double energy0;      // sum V (E + e_g) before
     double energy1;      // and after
     int abort;           // set by a block whose inter-block wait timed out
-    int pad[3];
+    int levels;          // levels of the multigrid hierarchy of this solve
+    long long t_start;   // device clock (ns): solve entry, preconditioner built, solve end
+    long long t_built;
+    long long t_end;
 };
 
 // Geometry of a plan in device memory (FP64).  Face arrays:
@@ -65,6 +68,59 @@ struct MGHierarchy {
     double* p64s;               // FP64 path: second direction buffer unused (reserved)
 };
 
+// Classical algebraic multigrid (preconditioner GQ_PRECOND_AMG).  Level 0 is the fine
+// system; level l+1 consists of the C-points of a PMIS splitting of level l (strength
+// measured on the unscaled operator), P_l is direct interpolation truncated to kAmgPmax
+// coarse points per row, and A_{l+1} = P_l^T A_l P_l (FP64, unscaled).  The cycle runs
+// on the Jacobi-scaled levels in FP32.  All sizes are decided on the device during the
+// set-up and written to AMGInfo; the arrays come from pools of fixed capacity (rows over
+// all levels, off-diagonal entries over all levels), and coarsening stops early when a
+// pool would overflow.
+constexpr int kAmgMaxLevels = 24;
+// largest grid (cells) of one plan: the multigrid entry pools (12 per cell) are int-indexed
+constexpr long long kMaxCells = 1ll << 27;
+constexpr int kAmgPmax = 4;          // interpolation entries per row (ELL layout)
+constexpr int kAmgRowMax = 64;       // distinct entries of one coarse row during the product
+
+struct AMGInfo {
+    int nlev;                        // levels built (1: level 0 only)
+    int stop;                        // why coarsening stopped (diagnostic)
+    int n[kAmgMaxLevels];            // rows of level l
+    int nnz[kAmgMaxLevels];          // off-diagonal entries of level l
+    int rnz[kAmgMaxLevels];          // entries of the restriction of level l -> l+1
+    int row_off[kAmgMaxLevels];      // first row of level l in the per-row pools
+    int nnz_off[kAmgMaxLevels];      // first entry of level l in the per-entry pools
+    int rnz_off[kAmgMaxLevels];      // first entry of R_l in the restriction pool
+    long long tns[kAmgMaxLevels + 2];  // device clock: start, fine copy done, level l coarsened
+};
+
+struct AMGData {
+    int n0;
+    int cap_rows;        // rows of all levels (level 0 included)
+    int cap_nnz;         // off-diagonal entries of all levels
+    AMGInfo* info;
+    int* rowptr;         // [cap_rows + kAmgMaxLevels]: level l at row_off[l] + l, entries relative to nnz_off[l]
+    int* col;            // [cap_nnz] column (row index within the level)
+    double* a64;         // [cap_nnz] unscaled off-diagonal entries
+    float* a32;          // [cap_nnz] Jacobi-scaled entries (levels >= 1)
+    unsigned char* sfl;  // [cap_nnz] strength: bit 0 row depends on column, bit 1 column depends on row
+    double* diag;        // [cap_rows] unscaled diagonal
+    double* s;           // [cap_rows] diag^{-1/2} (level 0: the workspace's dloc)
+    int* pc;             // [kAmgPmax cap_rows] P of level l -> l+1 (ELL): coarse column or -1
+    float* pv32;         // [kAmgPmax cap_rows] scaled interpolation weights
+    int* rrow;           // [cap_rows + kAmgMaxLevels] restriction rows (one per coarse row)
+    int* rent;           // [kAmgPmax cap_rows] restriction entries: index into the P pool
+    float *x, *b, *t;    // [cap_rows] cycle vectors (level 0 uses the Krylov buffers for b, x)
+    // set-up temporaries over the largest level (n0 rows)
+    double* pv64;        // [kAmgPmax n0] unscaled interpolation weights of the current level
+    double* rowmax;      // [n0]
+    double* wgt;         // [n0] PMIS weights
+    signed char *stA, *stB;  // [n0] C/F states
+    int *cidx, *cf, *cnt, *cnt2;  // [n0] coarse index, fine index of a coarse row, counts
+    double* dense;       // [kCoarseMax][2 kCoarseMax] Gauss-Jordan scratch
+    float* inv;          // [kCoarseMax][kCoarseMax] inverse of the coarsest level
+};
+
 // Workspace of one step in device memory.
 struct Workspace {
     // setup outputs (FP64); the scaled system overwrites some in place
@@ -80,6 +136,7 @@ struct Workspace {
     float *cW32, *cS32, *d32, *r32, *p32[2], *q32;
     // reductions, barrier, control
     MGHierarchy mg;
+    AMGData amg;
     double *partials;    // [2][max_blocks][kSlots]
     double *epart;       // [2][max_setup_blocks] energy partial sums (before, after)
     unsigned *bar;       // [2]
@@ -112,7 +169,7 @@ struct SolveParams {
     int max_iter, max_refine;
     double rtol, drop;
     long long spin_limit;
-    int precond;         // GQ_PRECOND_JACOBI or GQ_PRECOND_MG
+    int precond;         // GQ_PRECOND_JACOBI, GQ_PRECOND_MG or GQ_PRECOND_AMG
     float mg_omega;      // Jacobi smoothing weight of the V-cycle
     float mg_over;       // coarse-correction over-relaxation
     int pad;
@@ -197,4 +254,5 @@ struct gq_fld_plan {
     gq::Workspace ws;
     gq::SolveCtl* ctl_host;  // pinned
     cudaEvent_t ev[4];       // phase timing
+    int last_precond;        // preconditioner of the last step (-1: none yet)
 };

@@ -20,9 +20,35 @@
 namespace gq {
 namespace {
 
-struct MGShared {
+// level table of the algebraic hierarchy, kept per block (every block derives the same
+// sizes from the team-wide scans), and scan scratch
+struct AMGShared {
+    int nlev, stop;
+    int n[kAmgMaxLevels], nnz[kAmgMaxLevels], rnz[kAmgMaxLevels];
+    int row_off[kAmgMaxLevels], nnz_off[kAmgMaxLevels], rnz_off[kAmgMaxLevels];
+    long long red[32];
+    int wsc[32];
+    long long tns[kAmgMaxLevels + 2];
+};
+
+struct GJShared {
     double a[kCoarseMax][2 * kCoarseMax];   // Gauss-Jordan tableau of the coarsest level
     double col[kCoarseMax];                 // pivot column, read before it is eliminated
+};
+
+// per-warp column table of one coarse row of the algebraic Galerkin product
+struct RapShared {
+    double tval[kSolveThreads / 32][kAmgRowMax];
+    double sv[kSolveThreads / 32][32];
+    int tcol[kSolveThreads / 32][kAmgRowMax];
+};
+
+struct MGShared {
+    union {                                 // never in use at the same time
+        GJShared gj;
+        RapShared rap;
+    };
+    AMGShared amg;
 };
 
 // iteration range of a level: the whole team, or one block
@@ -105,26 +131,26 @@ __device__ void mg_dense_inverse(const MGHierarchy& mg, const Workspace& w, MGSh
                 cw = lvl0 ? __ldcg(w.wS + hi) : __ldcg(L.wS + hi) * __ldcg(L.s + hi) * __ldcg(L.s + lo);
             v = -cw;
         }
-        sm.a[r][c] = v;
+        sm.gj.a[r][c] = v;
     }
     __syncthreads();
     for (int p = 0; p < n; p++) {
-        const double piv = sm.a[p][p];
+        const double piv = sm.gj.a[p][p];
         __syncthreads();
-        for (int c = threadIdx.x; c < 2 * n; c += blockDim.x) sm.a[p][c] /= piv;
-        for (int r = threadIdx.x; r < n; r += blockDim.x) sm.col[r] = sm.a[r][p];
+        for (int c = threadIdx.x; c < 2 * n; c += blockDim.x) sm.gj.a[p][c] /= piv;
+        for (int r = threadIdx.x; r < n; r += blockDim.x) sm.gj.col[r] = sm.gj.a[r][p];
         __syncthreads();
         // every multiplier comes from the snapshot, so no thread reads an entry another
         // thread of this step writes
         for (int e = threadIdx.x; e < n * 2 * n; e += blockDim.x) {
             const int r = e / (2 * n), c = e - r * 2 * n;
-            if (r != p) sm.a[r][c] -= sm.col[r] * sm.a[p][c];
+            if (r != p) sm.gj.a[r][c] -= sm.gj.col[r] * sm.gj.a[p][c];
         }
         __syncthreads();
     }
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const int r = e / n, c = e - r * n;
-        mg.inv[e] = static_cast<float>(sm.a[r][n + c]);
+        mg.inv[e] = static_cast<float>(sm.gj.a[r][n + c]);
     }
     __syncthreads();
 }

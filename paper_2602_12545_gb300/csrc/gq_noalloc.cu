@@ -162,7 +162,7 @@ gq_status gq_fld_step_noalloc(int nx, int ny, int coord, const double* x_faces, 
         std::memset(info, 0, sizeof(*info));
         info->status = GQ_ERR_INVALID_ARG;
     }
-    if (nx < 1 || ny < 1 || (long long)nx * ny > (1ll << 30) || !x_faces || !y_faces) return GQ_ERR_INVALID_ARG;
+    if (nx < 1 || ny < 1 || (long long)nx * ny > gq::kMaxCells || !x_faces || !y_faces) return GQ_ERR_INVALID_ARG;
     if (coord != GQ_CARTESIAN && coord != GQ_SPHERICAL_POLAR) return GQ_ERR_INVALID_ARG;
     int dev = -1, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return GQ_ERR_CUDA;

@@ -183,17 +183,20 @@ __device__ __forceinline__ bool allreduce(double (&v)[NSUM + NMAX], double* part
 }  // namespace gq
 
 #include "gq_mg.cuh"
+#include "gq_amg.cuh"
 
 namespace gq {
 namespace {
 
 // Solve of one problem by one team of co-resident blocks, W cells per thread and pass;
-// MG selects the multigrid preconditioner (otherwise Jacobi, i.e. plain CG on A^).
+// PC selects the preconditioner: 0 Jacobi (plain CG on A^), 1 aggregation multigrid,
+// 2 algebraic multigrid.
 // Returns false when a wait of the team timed out (the caller must leave the kernel).
-template <bool MIXED, int W, bool MG>
+template <bool MIXED, int W, int PC>
 __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspace& w, Team team, RedShared& sh,
                                             MGShared& msh) {
     using R = std::conditional_t<MIXED, float, double>;
+    constexpr bool MG = PC != 0;
     const int N = P.N, nx = P.nx;
     const int nchunk = N / W;          // N is a multiple of W because nx is
     const int tid = team.rank * blockDim.x + threadIdx.x;
@@ -225,16 +228,28 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
         if (tid == 0) ctl->status = (flags & 2) ? kErrNonfinite : kErrInvalid;
         return true;
     }
+    if (tid == 0) ctl->t_start = global_ns();
     // multigrid: the rest of the hierarchy, the FP32 level-0 right-hand side and the two
     // preconditioned-residual buffers
     float* r0 = MIXED ? w.r32 : w.mg.r32;
     float* zc = w.mg.z;
     float* zo = w.mg.zold;
-    if constexpr (MG) {
+    if constexpr (PC == 2) {
+        if (!amg_build(w, nx, N / nx, team, tid, stride, P.spin_limit, abort_flag, sh, msh, parity)) {
+            if (threadIdx.x == 0) atomicExch(&ctl->status, kErrTimeout);
+            return false;
+        }
+    } else if constexpr (MG) {
         if (!mg_build(w, team, tid, stride, P.spin_limit, abort_flag, msh)) {
             if (threadIdx.x == 0) atomicExch(&ctl->status, kErrTimeout);
             return false;
         }
+    }
+    if (tid == 0) {
+        ctl->t_built = global_ns();
+        if constexpr (PC == 2) ctl->levels = msh.amg.nlev;
+        else if constexpr (PC == 1) ctl->levels = w.mg.nlev;
+        else ctl->levels = 1;
     }
 
     // ---- FP64 residual r64 = b^ - A^ y and its norms ----------------------------------
@@ -413,8 +428,14 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
             if constexpr (MG) {
                 // ---- z = V-cycle(r) ; r.z and r.z_old (Polak-Ribiere) ---------------------
                 double vz[2] = {0.0, 0.0};
-                if (!vcycle(w.mg, r0, zc, zo, P.mg_omega, P.mg_over, team, tid, stride, w.bar, P.spin_limit,
-                            abort_flag, &vz[0], &vz[1])) {
+                bool ok;
+                if constexpr (PC == 2)
+                    ok = amg_vcycle(w.amg, msh.amg, r0, zc, zo, w.cW32, w.cS32, nx, P.mg_omega, team, tid, stride,
+                                    w.bar, P.spin_limit, abort_flag, &vz[0], &vz[1]);
+                else
+                    ok = vcycle(w.mg, r0, zc, zo, P.mg_omega, P.mg_over, team, tid, stride, w.bar, P.spin_limit,
+                                abort_flag, &vz[0], &vz[1]);
+                if (!ok) {
                     timed_out = true;
                     break;
                 }
@@ -612,6 +633,7 @@ done:
         return false;
     }
     if (tid == 0) {
+        ctl->t_end = global_ns();
         ctl->status = status;
         ctl->iterations = it;
         ctl->refinements = nref;
@@ -626,17 +648,19 @@ __device__ __forceinline__ bool pcg_solve(const SolveParams& P, const Workspace&
                                           MGShared& msh) {
     constexpr int WV = MIXED ? 4 : 2;
     const bool vec = P.nx % WV == 0;
+    if (P.precond == GQ_PRECOND_AMG)
+        return vec ? pcg_solve_w<MIXED, WV, 2>(P, w, team, sh, msh) : pcg_solve_w<MIXED, 1, 2>(P, w, team, sh, msh);
     if (P.precond == GQ_PRECOND_MG)
-        return vec ? pcg_solve_w<MIXED, WV, true>(P, w, team, sh, msh) : pcg_solve_w<MIXED, 1, true>(P, w, team, sh, msh);
-    return vec ? pcg_solve_w<MIXED, WV, false>(P, w, team, sh, msh) : pcg_solve_w<MIXED, 1, false>(P, w, team, sh, msh);
+        return vec ? pcg_solve_w<MIXED, WV, 1>(P, w, team, sh, msh) : pcg_solve_w<MIXED, 1, 1>(P, w, team, sh, msh);
+    return vec ? pcg_solve_w<MIXED, WV, 0>(P, w, team, sh, msh) : pcg_solve_w<MIXED, 1, 0>(P, w, team, sh, msh);
 }
 
 // out-of-line copies for the batched kernel, which holds all the variants: separate
 // functions keep each variant's registers to itself
-template <bool MIXED, int W, bool MG>
+template <bool MIXED, int W, int PC>
 __device__ __noinline__ bool pcg_solve_call(const SolveParams& P, const Workspace& w, Team team, RedShared& sh,
                                             MGShared& msh) {
-    return pcg_solve_w<MIXED, W, MG>(P, w, team, sh, msh);
+    return pcg_solve_w<MIXED, W, PC>(P, w, team, sh, msh);
 }
 
 template <bool MIXED>
@@ -644,11 +668,14 @@ __device__ __forceinline__ bool pcg_solve_outlined(const SolveParams& P, const W
                                                    RedShared& sh, MGShared& msh) {
     constexpr int WV = MIXED ? 4 : 2;
     const bool vec = P.nx % WV == 0;
+    if (P.precond == GQ_PRECOND_AMG)
+        return vec ? pcg_solve_call<MIXED, WV, 2>(P, w, team, sh, msh)
+                   : pcg_solve_call<MIXED, 1, 2>(P, w, team, sh, msh);
     if (P.precond == GQ_PRECOND_MG)
-        return vec ? pcg_solve_call<MIXED, WV, true>(P, w, team, sh, msh)
-                   : pcg_solve_call<MIXED, 1, true>(P, w, team, sh, msh);
-    return vec ? pcg_solve_call<MIXED, WV, false>(P, w, team, sh, msh)
-               : pcg_solve_call<MIXED, 1, false>(P, w, team, sh, msh);
+        return vec ? pcg_solve_call<MIXED, WV, 1>(P, w, team, sh, msh)
+                   : pcg_solve_call<MIXED, 1, 1>(P, w, team, sh, msh);
+    return vec ? pcg_solve_call<MIXED, WV, 0>(P, w, team, sh, msh)
+               : pcg_solve_call<MIXED, 1, 0>(P, w, team, sh, msh);
 }
 
 template <bool MIXED>

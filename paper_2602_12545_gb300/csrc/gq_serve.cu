@@ -180,7 +180,7 @@ gq_status gq_server_submit(gq_server* S, const gq_request* rq, int64_t* id_out) 
     const gq_grid_desc& g = rq->grid;
     if (g.nx < 1 || g.ny < 1 || !g.x_faces || !g.y_faces || !rq->rho || !rq->e_g || !rq->E_r || rq->n_steps < 1)
         return GQ_ERR_INVALID_ARG;
-    if ((long long)g.nx * g.ny > (1ll << 30)) return GQ_ERR_INVALID_ARG;
+    if ((long long)g.nx * g.ny > gq::kMaxCells) return GQ_ERR_INVALID_ARG;
     const size_t need = gq_server_request_bytes(g.nx, g.ny);
     if (need == 0) return GQ_ERR_CUDA;
     if (need > S->opts.budget_bytes) return GQ_ERR_BUDGET;

@@ -196,7 +196,7 @@ __device__ void scale_body(const StepParams& sp, const Workspace& w, int blk, in
         w.wS[k] = cs;
         w.rhs[k] *= sk;
         w.y[k] = sp.E[k] / sk;
-        if (sp.mixed || sp.precond == GQ_PRECOND_MG) {
+        if (sp.mixed || sp.precond != GQ_PRECOND_JACOBI) {
             w.cW32[k] = static_cast<float>(cw);
             w.cS32[k] = static_cast<float>(cs);
         }

@@ -35,7 +35,7 @@ class SolverOptions:
     spin_limit: int = 0
     restart: int = 0
     timing: int = 0
-    precond: int = 1              # 0 Jacobi, 1 aggregation multigrid V-cycle
+    precond: int = 1              # 0 Jacobi, 1 aggregation multigrid, 2 algebraic multigrid
     mg_omega: float = 0.0         # 0 = library default
     mg_over: float = 0.0
 
@@ -78,6 +78,15 @@ class FLDPlan:
     @property
     def nbytes(self) -> int:
         return int(N.load().gq_fld_plan_bytes(self._h))
+
+    def precond_info(self) -> dict:
+        """gq_fld_precond_info: the multigrid hierarchy of the last step (levels, rows,
+        entries, device build times)."""
+        out = N.PrecondInfo()
+        rc = N.load().gq_fld_precond_info(self._h, ctypes.byref(out))
+        if rc != N.GQ_OK:
+            raise N.GQError(rc, "gq_fld_precond_info")
+        return out.as_dict()
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
