@@ -47,6 +47,26 @@ BYTES_VCYCLE = (4 * 16 + 8 + 4) * 4.0 / 3.0 + 4
 BYTES_ITER_MG = {1: 32.0 + BYTES_VCYCLE, 0: 64.0 + BYTES_VCYCLE + 4.0}
 BYTES_RESID = {1: 60.0, 0: 40.0}      # FP64 residual (c_W, c_S, b, y in; r out) [+ y += d for mixed]
 KERNELS_PER_STEP = 7                  # cells, faces, diag, scale, pcg, backsub, finalize
+PRECOND_NAMES = {0: "Jacobi", 1: "aggregation multigrid V-cycle (FP32)",
+                 2: "algebraic multigrid V-cycle (FP32), hierarchy built on the device every step"}
+# default preconditioner per workload: the smooth spherical field converges fastest with
+# the 2 x 2 aggregation cycle; i.i.d. fields (config-0 statistics) need the algebraic one
+DEFAULT_PRECOND = {"c2": 1, "c1": 2, "c0": 2, "batched": 2, "serving": 2}
+
+
+def amg_cycle_bytes(pi: dict, n0: int) -> float:
+    """Algorithmic bytes of one algebraic V-cycle per fine cell, from the hierarchy the
+    device built: level 0 (structured, FP32) 4 sweep/residual passes of 20 B and the
+    transfers (P in ELL: 32 B, plus values) 120 B per cell; every coarse level applies its
+    CSR operator 4 times (row pointer 4 B, column + value 8 B per entry) and moves its
+    vectors (44 B per row); transfers 60 B per row of every level but the coarsest."""
+    rows, ents = pi["rows"], pi["entries"]
+    b = 120.0 * rows[0]
+    for l in range(1, len(rows)):
+        b += 60.0 * rows[l] + 32.0 * ents[l]
+    for l in range(len(rows) - 1):
+        b += 60.0 * rows[l]
+    return b / n0
 # cell-wise residual target of the spherical workload: the loosest setting whose E and T
 # agree with the tightly solved FP64 answer to 1e-8 per cell (reported in the line)
 DEFAULT_C2_RTOL = 1e-11
@@ -64,11 +84,15 @@ def parse():
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: mean arrival rate (1/s)")
     ap.add_argument("--budget-gb", type=float, default=60.0, help="serving: device memory budget")
     ap.add_argument("--rtol", type=float, default=None)
-    ap.add_argument("--precond", type=int, default=1, help="1 multigrid V-cycle (default), 0 Jacobi")
+    ap.add_argument("--precond", type=int, default=None,
+                    help="0 Jacobi, 1 aggregation multigrid, 2 algebraic multigrid (default: per workload)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison path")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.precond is None:
+        args.precond = DEFAULT_PRECOND[args.workload]
+    return args
 
 
 def workload(name):
@@ -277,7 +301,13 @@ def run_ours(args):
     t_solve = statistics.mean(i["t_solve_ms"] for i in infos)
     t_setup = statistics.mean(i["t_setup_ms"] for i in infos)
     t_finish = statistics.mean(i["t_finish_ms"] for i in infos)
-    b_iter = BYTES_ITER_MG[prec] if args.precond == 1 else BYTES_ITER[prec]
+    t_pre = statistics.mean(i["t_precond_ms"] for i in infos)
+    if args.precond == 2:
+        b_iter = BYTES_ITER[prec] + 4.0 + amg_cycle_bytes(plan.precond_info(), N)
+    elif args.precond == 1:
+        b_iter = BYTES_ITER_MG[prec]
+    else:
+        b_iter = BYTES_ITER[prec]
     alg_bytes = N * (its * b_iter + (refs + 1) * BYTES_RESID[prec])
     achieved = alg_bytes / (t_solve / 1e3) / 1e9
     peak, peak_kind = peaks()
@@ -338,14 +368,16 @@ def run_ours(args):
         "config": {"workload": f"{P.name}_{'mixed' if prec else 'fp64'}", "grid": desc, "nx": P.nx, "ny": P.ny,
                    "cells": N, "precision": "FP32 inner PCG + FP64 refinement" if prec else "FP64 PCG",
                    "rtol": rtol, "residual": "cell-wise max |b-Ax|_k/(A_kk x_k) of the reduced system",
-                   "preconditioner": "aggregation multigrid V-cycle (FP32)" if args.precond == 1 else "Jacobi",
+                   "preconditioner": PRECOND_NAMES[args.precond],
                    "l2": "inputs restored and L2 flushed (512 MiB write) before every step, outside the timed events",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "step_latency_ms": {"p50": p50, "p99": p99},
         "solver": {"iterations": its, "refinements": refs, "rel_residual": infos[-1]["rel_residual"],
                    "rel_residual_l2": infos[-1]["rel_residual_l2"], "max_rel_err_E_vs_fp64_tight": err_E,
                    "max_rel_err_T_vs_fp64_tight": err_T, "t_setup_ms": t_setup, "t_solve_ms": t_solve,
-                   "t_finish_ms": t_finish, "solve_blocks": infos[-1]["solve_blocks"]},
+                   "t_finish_ms": t_finish, "t_precond_build_ms": t_pre,
+                   "t_per_iteration_us": statistics.mean(i["t_iter_us"] for i in infos),
+                   "precond_levels": infos[-1]["precond_levels"], "solve_blocks": infos[-1]["solve_blocks"]},
         "roofline": {"kernel": "k_pcg (persistent cooperative Krylov solve)", "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": peak_kind, "traffic": traffic,
@@ -432,7 +464,7 @@ def run_batched(args):
     line = _batch_line(args, world, world * cells * args.steps / (total_ms / 1e3), total_ms, infos, {
         "config": {"workload": f"c3_batch{len(probs)}_mixed", "problems": len(probs), "cells": cells,
                    "sides": "nx, ny log-uniform in [32, 512], Cartesian and spherical-polar alternating",
-                   "rtol": probs[0].rtol, "preconditioner": "multigrid" if args.precond == 1 else "Jacobi",
+                   "rtol": probs[0].rtol, "preconditioner": PRECOND_NAMES[args.precond],
                    "l2": "inputs restored and L2 flushed before every step, outside the timed events",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "batch": {"autotuned": tuned, "autotune_s": t_tune, "graph": B.uses_graph,
@@ -490,7 +522,7 @@ def run_serving(args):
         "config": {"workload": f"c4_serving_{args.requests}req_{int(args.rate)}per_s", "requests": args.requests,
                    "rate_per_s": args.rate, "sides": "square, log-uniform in [64, 2048]", "steps_per_request": 10,
                    "budget_gb": args.budget_gb, "rtol": 1e-8,
-                   "preconditioner": "multigrid" if args.precond == 1 else "Jacobi"},
+                   "preconditioner": PRECOND_NAMES[args.precond]},
         "serving": {k: v for k, v in out.items()},
         "latency_s": {"p50": out["latency_p50_s"], "p99": out["latency_p99_s"]},
         "one_at_a_time_fp64": {"value": cells_seq / t_seq, "unit": UNIT, "requests_sampled": len(sample)},

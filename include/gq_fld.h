@@ -93,15 +93,16 @@ typedef struct { int side[4]; } gq_bc;
  *               iterative refinement), 0 keeps the search direction (default).
  *   timing      1 records CUDA events around the set-up, solve and finish phases on the
  *               stream and reports their durations in gq_step_info (0 = off).
- *   precond     GQ_PRECOND_MG (default): CG preconditioned by one V-cycle of aggregation
- *               multigrid (2 x 2 Galerkin coarsening of the Jacobi-scaled operator, two
- *               weighted-Jacobi sweeps before and after, exact solve of the coarsest
- *               <= 32 cells), in FP32 for both precisions, with Polak-Ribiere directions.
- *               GQ_PRECOND_AMG: one V-cycle of classical algebraic multigrid, built on
- *               the device every step (PMIS coarsening with strength taken on the
- *               unscaled operator, direct interpolation truncated to 4 entries, Galerkin
- *               coarse operators), robust where the face weights jump by orders of
- *               magnitude from cell to cell; FP32 cycle for both precisions.
+ *   precond     GQ_PRECOND_AMG (default): CG preconditioned by one V-cycle of classical
+ *               algebraic multigrid, built on the device every step (PMIS coarsening with
+ *               strength taken on the unscaled operator, direct interpolation truncated
+ *               to 4 entries, Galerkin coarse operators), robust where the face weights
+ *               jump by orders of magnitude from cell to cell; FP32 cycle for both
+ *               precisions, Polak-Ribiere directions.
+ *               GQ_PRECOND_MG: one V-cycle of aggregation multigrid (2 x 2 Galerkin
+ *               coarsening of the Jacobi-scaled operator, two weighted-Jacobi sweeps
+ *               before and after, exact solve of the coarsest <= 32 cells); cheapest per
+ *               step on smooth fields.
  *               GQ_PRECOND_JACOBI: diagonal (Jacobi) preconditioning only.
  *   mg_omega    Jacobi smoothing weight of the V-cycle, in (0, 1] (0 = default 0.8).
  *   mg_over     coarse-correction factor, in (0, 2) (0 = default 1.5; the AMG cycle
@@ -203,7 +204,7 @@ gq_status gq_fld_precond_info(const gq_fld_plan *plan, gq_precond_info *out);
  * bytes (32 MiB) that each GPU loading the library holds until the process exits; the call
  * makes no cudaMalloc / cudaFree / allocating call.  The caller passes inputs and outputs:
  * x_faces (nx+1) and y_faces (ny+1) as DEVICE arrays, the fields as in gq_fld_step (no
- * explicit areas or volumes).  Grids whose footprint exceeds the array (about 160 000 cells)
+ * explicit areas or volumes).  Grids whose footprint exceeds the array (about 50 000 cells)
  * return GQ_ERR_INVALID_ARG before any work.  All calls on a device share the array and it
  * keeps the previous call's contents; the call resets what must start at zero, and calls
  * that overlap on the GPU (other streams or host threads) race: serialise them.  The first
@@ -369,8 +370,8 @@ size_t gq_server_used_bytes(gq_server *server);
 void gq_server_destroy(gq_server *server);
 
 /* Default solver options: FP64, LP limiter, rtol 1e-10, max_iter 200000, inner_rtol 0.1,
- * max_refine 200, default spin limit, keep the search direction, multigrid
- * preconditioning (omega 0.8, coarse factor 1.5). */
+ * max_refine 200, default spin limit, keep the search direction, algebraic multigrid
+ * preconditioning (omega 0.8; coarse factor 1.5 for the aggregation cycle). */
 void gq_solver_opts_default(gq_solver_opts *opts);
 
 /* Static description of a status code. */

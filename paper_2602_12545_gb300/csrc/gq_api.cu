@@ -408,7 +408,7 @@ void gq_solver_opts_default(gq_solver_opts* o) {
     o->spin_limit = 0;
     o->restart = 0;
     o->timing = 0;
-    o->precond = GQ_PRECOND_MG;
+    o->precond = GQ_PRECOND_AMG;
     o->mg_omega = 0.8;
     o->mg_over = 1.5;
 }

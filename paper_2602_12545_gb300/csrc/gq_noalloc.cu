@@ -11,7 +11,7 @@
 //
 // Limits and rules:
 //   - The array holds kNoAllocBytes (32 MiB) per device that loads the library, for the
-//     life of the process.  Grids whose footprint exceeds it (about 160 000 cells) are
+//     life of the process.  Grids whose footprint exceeds it (about 50 000 cells) are
 //     rejected with GQ_ERR_INVALID_ARG before anything runs.
 //   - Every call on a device shares the one array, which keeps the previous call's
 //     contents; the call clears what must start at zero.  Calls that overlap on the GPU

@@ -35,7 +35,7 @@ class SolverOptions:
     spin_limit: int = 0
     restart: int = 0
     timing: int = 0
-    precond: int = 1              # 0 Jacobi, 1 aggregation multigrid, 2 algebraic multigrid
+    precond: int = 2              # 0 Jacobi, 1 aggregation multigrid, 2 algebraic multigrid
     mg_omega: float = 0.0         # 0 = library default
     mg_over: float = 0.0
 

@@ -141,7 +141,7 @@ def test_small_grids(fld, orc, nx, ny, coord, prec):
     ref = orc.step(P, "lu")
     cond = componentwise_condition(orc, P, ref["E_r"])
     rtol = 1e-12 if prec == W.PREC_FP64 else 1e-10
-    out = run_gpu(fld, P, prec, rtol)
+    out = run_gpu(fld, P, prec, rtol, precond=1)      # aggregation multigrid (AMG: test_gpu_amg)
     # GQ_ERR_NOT_CONVERGED is the documented answer when rtol lies below the FP64 floor
     # of the cell-wise residual (ill-conditioned draws); the iterate must still agree
     assert out["info"]["status"] in (0, 4), out["info"]
