@@ -357,8 +357,11 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        it_fp64 = int(fp64["iterations"]) if fp64 else int(its)
-        cpu, _ = oracle_sample(P, it_fp64)
+        # the oracle's solver is Jacobi-PCG: extrapolate to the iteration count that method
+        # needs at this tolerance (taken from the GPU's FP64 Jacobi path, untimed)
+        j_info = one(F.SolverOptions(prec=0, limiter=P.limiter, rtol=rtol, timing=0, precond=0,
+                                     max_iter=1000000), check=False)
+        cpu, _ = oracle_sample(P, int(j_info["iterations"]))
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
