@@ -192,6 +192,11 @@ typedef struct {
     float build_ms[24];         /* AMG: coarsening level l into level l + 1 */
     float fine_copy_ms;         /* AMG: copy of the fine operator into the hierarchy */
     float coarsest_ms;          /* AMG: inverse of the coarsest level */
+    float build_phase_ms[8];    /* AMG: build time per phase summed over the levels (strength,
+                                   splitting rounds, numbering, interpolation, product count,
+                                   scans, product fill, scaling) */
+    float cycle_ms[24];         /* AMG: time per level summed over the solve's cycles; the last
+                                   entry is the time outside the cycle (Krylov updates) */
 } gq_precond_info;
 
 gq_status gq_fld_precond_info(const gq_fld_plan *plan, gq_precond_info *out);

@@ -67,14 +67,16 @@ class StepInfo(ctypes.Structure):
 class PrecondInfo(ctypes.Structure):
     _fields_ = [("precond", ctypes.c_int), ("levels", ctypes.c_int), ("stop_reason", ctypes.c_int),
                 ("rows", ctypes.c_int * 24), ("entries", ctypes.c_int * 24), ("build_ms", ctypes.c_float * 24),
-                ("fine_copy_ms", ctypes.c_float), ("coarsest_ms", ctypes.c_float)]
+                ("fine_copy_ms", ctypes.c_float), ("coarsest_ms", ctypes.c_float),
+                ("build_phase_ms", ctypes.c_float * 8), ("cycle_ms", ctypes.c_float * 24)]
 
     def as_dict(self) -> dict:
         n = self.levels
         return {"precond": self.precond, "levels": n, "stop_reason": self.stop_reason,
                 "rows": list(self.rows[:n]), "entries": list(self.entries[:n]),
                 "build_ms": list(self.build_ms[:max(n - 1, 0)]), "fine_copy_ms": self.fine_copy_ms,
-                "coarsest_ms": self.coarsest_ms}
+                "coarsest_ms": self.coarsest_ms, "build_phase_ms": list(self.build_phase_ms),
+                "cycle_ms": list(self.cycle_ms[:n]), "outside_cycle_ms": self.cycle_ms[23]}
 
 
 class BatchItem(ctypes.Structure):

@@ -363,6 +363,14 @@ __device__ int amg_level(int l, const Workspace& w, Team tm, int tid, int stride
     const double* dg = A.diag + ro;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int gw = tid >> 5, nwarps = stride >> 5;
+    auto mark = [&](int k) {
+        if (threadIdx.x == 0) {
+            const long long t = global_ns();
+            as.bph[k] += t - as.tlast;
+            as.tlast = t;
+        }
+    };
+    if (threadIdx.x == 0) as.tlast = global_ns();
 
     // 1. largest negative coupling of every row
     for (int i = tid; i < n; i += stride) {
@@ -391,6 +399,7 @@ __device__ int amg_level(int l, const Workspace& w, Team tm, int tid, int stride
         A.cnt2[i] = nS;
     }
     if (!sync()) return kLvlTimeout;
+    mark(0);
     // 3. PMIS rounds (stA -> stB -> stA)
     for (int round = 0; round < kAmgRounds; round++) {
         for (int i = tid; i < n; i += stride) {
@@ -426,6 +435,7 @@ __device__ int amg_level(int l, const Workspace& w, Team tm, int tid, int stride
         if (!allreduce<1, 0>(cu, w.partials, parity, w.bar, spin, abort_flag, sh, tm)) return kLvlTimeout;
         if (cu[0] == 0.0) break;
     }
+    mark(1);
     // 4. undecided points become C; an F point that depends on points but on no C point
     //    becomes C (stA -> stB); C flags for the numbering
     for (int i = tid; i < n; i += stride) {
@@ -449,6 +459,7 @@ __device__ int amg_level(int l, const Workspace& w, Team tm, int tid, int stride
     int nc = 0;
     if (!team_scan(A.cnt, A.cidx, n, nc, w.partials, parity, w.bar, spin, abort_flag, tm, as)) return kLvlTimeout;
     if (!sync()) return kLvlTimeout;
+    mark(2);
     if (nc == 0 || nc >= n) {
         if (threadIdx.x == 0) as.stop = kAmgStopNoC;
         return kLvlStop;
@@ -517,6 +528,7 @@ __device__ int amg_level(int l, const Workspace& w, Team tm, int tid, int stride
         }
     }
     if (!sync()) return kLvlTimeout;
+    mark(3);
     // 7. sizes of the coarse rows and of the restriction rows: one thread per row (one warp
     //    per row when a row is too long for a thread's table)
     bool warp_rap = false;
@@ -551,6 +563,7 @@ __device__ int amg_level(int l, const Workspace& w, Team tm, int tid, int stride
             return kLvlStop;
         }
     }
+    mark(4);
     // 8. row pointers of level l+1 and of the restriction
     int nnz_c = 0, rtot = 0;
     int* rp_c = A.rowptr + ro_c + (l + 1);
@@ -568,6 +581,7 @@ __device__ int amg_level(int l, const Workspace& w, Team tm, int tid, int stride
         rr_c[nc] = rtot;
     }
     if (!sync()) return kLvlTimeout;
+    mark(5);
     // 9. fill level l+1 and the restriction of level l (the same method as the count)
     if (warp_rap) {
         for (int c = gw; c < nc; c += nwarps) {
@@ -585,6 +599,7 @@ __device__ int amg_level(int l, const Workspace& w, Team tm, int tid, int stride
         }
     }
     if (!sync()) return kLvlTimeout;
+    mark(6);
     // 10. scaling of level l+1
     for (int c = tid; c < nc; c += stride) A.s[ro_c + c] = 1.0 / sqrt(ldp<CG>(A.diag + ro_c + c));
     if (threadIdx.x == 0) {
@@ -615,6 +630,7 @@ __device__ int amg_level(int l, const Workspace& w, Team tm, int tid, int stride
         }
     }
     if (!sync()) return kLvlTimeout;
+    mark(7);
     if (threadIdx.x == 0) as.tns[2 + l] = global_ns();
     return kLvlOk;
 }
@@ -630,7 +646,10 @@ __device__ bool amg_build(const Workspace& w, int nx, int ny, Team team, int tid
     AMGShared& as = msh.amg;
     const int n0 = A.n0;
     auto sync = [&]() { return team_barrier(w.bar, team, spin, abort_flag); };
-    if (threadIdx.x == 0) as.tns[0] = global_ns();
+    if (threadIdx.x == 0) {
+        as.tns[0] = global_ns();
+        for (int k = 0; k < 8; k++) as.bph[k] = 0;
+    }
 
     // ---- level 0 ------------------------------------------------------------------------
     for (int i = tid; i < n0; i += stride) {
@@ -748,6 +767,7 @@ __device__ bool amg_build(const Workspace& w, int nx, int ny, Team team, int tid
             AMGInfo* I = A.info;
             as.tns[as.nlev + 1] = global_ns();
             for (int k = 0; k <= as.nlev + 1; k++) I->tns[k] = as.tns[k];
+            for (int k = 0; k < 8; k++) I->bph[k] = as.bph[k];
             I->nlev = as.nlev;
             I->stop = as.stop;
             for (int k = 0; k < as.nlev; k++) {
@@ -774,8 +794,31 @@ __device__ bool amg_build(const Workspace& w, int nx, int ny, Team team, int tid
             as.rnz_off[k] = __ldcg(&I->rnz_off[k]);
         }
     }
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < kAmgMaxLevels; k++) as.cyc[k] = 0;
+        as.tcyc = global_ns();
+        as.ccur = kAmgMaxLevels - 1;
+    }
     __syncthreads();
     return true;
+}
+
+// cycle timing: the time since the last mark goes to the slot then current (block 0's
+// first thread only; the last slot collects the time outside the cycle)
+__device__ __forceinline__ void cyc_mark(AMGShared& as, Team team, int slot) {
+    if (team.rank == 0 && threadIdx.x == 0) {
+        const long long t = global_ns();
+        as.cyc[as.ccur] += t - as.tcyc;
+        as.tcyc = t;
+        as.ccur = slot;
+    }
+}
+
+// writes the cycle timing of the solve to the device info block
+__device__ void amg_cycle_report(const AMGData& A, AMGShared& as, Team team) {
+    cyc_mark(as, team, kAmgMaxLevels - 1);
+    if (team.rank == 0 && threadIdx.x == 0)
+        for (int k = 0; k < kAmgMaxLevels; k++) A.info->cyc[k] = as.cyc[k];
 }
 
 // ---- V-cycle (FP32) -------------------------------------------------------------------
@@ -941,7 +984,7 @@ __device__ void amg_coarse(const AV& L, const float* inv, bool dense, float om, 
 
 // z = B r0 on the team; rz, rzo receive this thread's partial sums of r0.z and r0.z_old.
 // Returns false on a timed-out wait.
-__device__ bool amg_vcycle(const AMGData& A, const AMGShared& as, const float* r0, float* z, const float* zold,
+__device__ bool amg_vcycle(const AMGData& A, AMGShared& as, const float* r0, float* z, const float* zold,
                            const float* cW0, const float* cS0, int nx0, float om, Team team, int tid, int stride,
                            unsigned* bar, long long spin, int* abort_flag, double* rz, double* rzo) {
     const int nl = as.nlev;
@@ -959,6 +1002,7 @@ __device__ bool amg_vcycle(const AMGData& A, const AMGShared& as, const float* r
 
     for (int l = 0; l < lg; l++) {
         const AV F = view(l), C = view(l + 1);
+        cyc_mark(as, team, l);
         amg_pre<true, true>(F, om, tr);
         if (!sync()) return false;
         amg_resid<true, true>(F, tr);
@@ -986,6 +1030,7 @@ __device__ bool amg_vcycle(const AMGData& A, const AMGShared& as, const float* r
     } else if (team.rank == 0) {
         for (int l = lg; l < Lc; l++) {
             const AV F = view(l), C = view(l + 1);
+            cyc_mark(as, team, l);
             if (l == lg) amg_pre<false, true>(F, om, br);
             else amg_pre<false, false>(F, om, br);
             __syncthreads();
@@ -996,10 +1041,12 @@ __device__ bool amg_vcycle(const AMGData& A, const AMGShared& as, const float* r
             __syncthreads();
         }
         const AV Z = view(Lc);
+        cyc_mark(as, team, Lc);
         amg_coarse(Z, A.inv, dense, om, br, zold, Lc == 0 ? rz : nullptr, rzo);
         __syncthreads();
         for (int l = Lc - 1; l >= lg; l--) {
             const AV F = view(l), C = view(l + 1);
+            cyc_mark(as, team, l);
             amg_prolong<false>(F, C, br);
             __syncthreads();
             if (l == lg) {
@@ -1017,6 +1064,7 @@ __device__ bool amg_vcycle(const AMGData& A, const AMGShared& as, const float* r
     if (!sync()) return false;
     for (int l = lg - 1; l >= 0; l--) {
         const AV F = view(l), C = view(l + 1);
+        cyc_mark(as, team, l);
         amg_prolong<true>(F, C, tr);
         if (!sync()) return false;
         amg_sweep<true, true>(F, F.x, F.t, om, tr, nullptr, nullptr, nullptr);
@@ -1024,6 +1072,7 @@ __device__ bool amg_vcycle(const AMGData& A, const AMGShared& as, const float* r
         amg_sweep<true, true>(F, F.t, F.x, om, tr, zold, l == 0 ? rz : nullptr, rzo);
         if (l > 0 && !sync()) return false;
     }
+    cyc_mark(as, team, kAmgMaxLevels - 1);
     return true;
 }
 

@@ -533,6 +533,8 @@ gq_status gq_fld_precond_info(const gq_fld_plan* P, gq_precond_info* out) {
         out->fine_copy_ms = (float)((I.tns[1] - I.tns[0]) * 1e-6);
         out->coarsest_ms = (float)((I.tns[nl + 1] - I.tns[nl]) * 1e-6);
     }
+    for (int k = 0; k < 8; k++) out->build_phase_ms[k] = (float)(I.bph[k] * 1e-6);
+    for (int k = 0; k < gq::kAmgMaxLevels && k < 24; k++) out->cycle_ms[k] = (float)(I.cyc[k] * 1e-6);
     return GQ_OK;
 }
 

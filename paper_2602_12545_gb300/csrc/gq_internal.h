@@ -92,6 +92,8 @@ struct AMGInfo {
     int nnz_off[kAmgMaxLevels];      // first entry of level l in the per-entry pools
     int rnz_off[kAmgMaxLevels];      // first entry of R_l in the restriction pool
     long long tns[kAmgMaxLevels + 2];  // device clock: start, fine copy done, level l coarsened
+    long long bph[8];                  // build time per phase, summed over the levels (ns)
+    long long cyc[kAmgMaxLevels];      // time per level over all cycles of the solve; last: the rest
 };
 
 struct AMGData {

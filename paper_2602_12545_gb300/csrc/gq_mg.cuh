@@ -29,6 +29,11 @@ struct AMGShared {
     long long red[32];
     int wsc[32];
     long long tns[kAmgMaxLevels + 2];
+    long long bph[8];                   // build time per phase (block 0's clock)
+    long long tlast;
+    long long cyc[kAmgMaxLevels];       // cycle time per level; the last slot: outside the cycle
+    long long tcyc;
+    int ccur;
 };
 
 struct GJShared {

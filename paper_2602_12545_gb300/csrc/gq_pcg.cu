@@ -628,6 +628,9 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
     }
 
 done:
+    if constexpr (PC == 2) {
+        if (!timed_out) amg_cycle_report(w.amg, msh.amg, team);
+    }
     if (timed_out) {
         if (threadIdx.x == 0) atomicExch(&ctl->status, kErrTimeout);
         return false;
