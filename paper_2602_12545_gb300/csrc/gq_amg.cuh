@@ -32,6 +32,9 @@ namespace gq {
 namespace {
 
 constexpr double kAmgTheta = 0.25;
+// levels of at most this many rows are built and cycled by the team's first block alone
+// (about where one block's sweep costs as much as a team barrier)
+constexpr int kAmgBlockMax = 1024;
 constexpr int kAmgRounds = 40;
 constexpr signed char kStU = 0, kStC = 1, kStF = 2;
 
@@ -278,20 +281,19 @@ __device__ bool amg_coarse_row_warp(int c, const AMGData& A, int ro, const int* 
 // false when the row has more than kAmgRowThread columns.
 constexpr int kAmgRowThread = 24;
 
-template <bool FILL, bool CG>
-__device__ bool amg_coarse_row_thread(int c, const AMGData& A, int ro, const int* rp, const int* cl,
-                                      const double* av, const double* dg, int* col_out, double* a_out,
-                                      double* diag_out, int* rent_out, int& ncol, int& nr) {
-    int cols[kAmgRowThread];
-    double vals[kAmgRowThread];
-    int m = 0;
-    double dgc = 0.0;
+// The coarse row's column table (cols, vals), its diagonal and its restriction count.
+template <bool CG>
+__device__ __forceinline__ bool amg_row_table(int c, const AMGData& A, int ro, const int* rp, const int* cl,
+                                              const double* av, const double* dg, int (&cols)[kAmgRowThread],
+                                              double (&vals)[kAmgRowThread], double& dgc, int& m, int& nr) {
+    m = 0;
+    dgc = 0.0;
     nr = 0;
     const int f = ldp<CG>(A.cf + c);
     const int fb = ldp<CG>(rp + f), fe = ldp<CG>(rp + f + 1);
     // contributors: f itself (slot 0, weight 1) and the F neighbours of f that interpolate from c
     for (int h = -1; h < fe - fb; h++) {
-        int i, slot = 0;
+        int i;
         double wi;
         if (h < 0) {
             i = f;
@@ -299,13 +301,12 @@ __device__ bool amg_coarse_row_thread(int c, const AMGData& A, int ro, const int
         } else {
             i = ldp<CG>(cl + fb + h);
             if (ldp<CG>(A.stB + i) != kStF) continue;
-            slot = -1;
+            int slot = -1;
             for (int q = 0; q < kAmgPmax; q++)
                 if (ldp<CG>(A.pc + (size_t)kAmgPmax * (ro + i) + q) == c) slot = q;
             if (slot < 0) continue;
             wi = ldp<CG>(A.pv64 + (size_t)kAmgPmax * i + slot);
         }
-        if constexpr (FILL) rent_out[nr] = kAmgPmax * (ro + i) + slot;
         nr++;
         const int ib = ldp<CG>(rp + i), ie = ldp<CG>(rp + i + 1);
         for (int e = ib - 1; e < ie; e++) {
@@ -334,15 +335,25 @@ __device__ bool amg_coarse_row_thread(int c, const AMGData& A, int ro, const int
             }
         }
     }
-    ncol = m;
-    if constexpr (FILL) {
-        for (int u = 0; u < m; u++) {
-            col_out[u] = cols[u];
-            a_out[u] = vals[u];
-        }
-        *diag_out = dgc;
-    }
     return true;
+}
+
+// the restriction entries of coarse row c (indices into the P pool), in contributor order
+template <bool CG>
+__device__ __forceinline__ void amg_row_rents(int c, const AMGData& A, int ro, const int* rp, const int* cl,
+                                              int* rent_out) {
+    const int f = ldp<CG>(A.cf + c);
+    const int fb = ldp<CG>(rp + f), fe = ldp<CG>(rp + f + 1);
+    rent_out[0] = kAmgPmax * (ro + f);
+    int nr = 1;
+    for (int h = 0; h < fe - fb; h++) {
+        const int i = ldp<CG>(cl + fb + h);
+        if (ldp<CG>(A.stB + i) != kStF) continue;
+        int slot = -1;
+        for (int q = 0; q < kAmgPmax; q++)
+            if (ldp<CG>(A.pc + (size_t)kAmgPmax * (ro + i) + q) == c) slot = q;
+        if (slot >= 0) rent_out[nr++] = kAmgPmax * (ro + i) + slot;
+    }
 }
 
 enum { kLvlOk = 0, kLvlStop = 1, kLvlTimeout = 2 };
@@ -527,26 +538,76 @@ __device__ int amg_level(int l, const Workspace& w, Team tm, int tid, int stride
             pvr[q] = kv[q];
         }
     }
+    if (tid == 0) {
+        A.info->ctr = 0;
+        A.info->rctr = 0;
+    }
     if (!sync()) return kLvlTimeout;
     mark(3);
-    // 7. sizes of the coarse rows and of the restriction rows: one thread per row (one warp
-    //    per row when a row is too long for a thread's table)
-    bool warp_rap = false;
-    double ovf[1] = {0.0};
-    if (!warp_rap) {
-        for (int c = tid; c < nc; c += stride) {
-            int m = 0, nr = 0;
-            if (!amg_coarse_row_thread<false, CG>(c, A, ro, rp, cl, av, dg, nullptr, nullptr, nullptr, nullptr, m,
-                                                   nr))
-                ovf[0] = 1.0;
+    // 7. the coarse rows of P^T A P, one thread per row, computed once: each row is staged
+    //    at the tail of the entry pool (its restriction entries at the tail of the
+    //    restriction pool), with space reserved per warp by one atomic; the final layout
+    //    follows from the scans, so the result does not depend on the reservation order.
+    //    A row too long for a thread's table sends the level to one warp per row (counted,
+    //    then filled); too little tail space to the thread count-and-fill.
+    const int eo_c = eo + as.nnz[l];
+    const int roff = as.rnz_off[l];
+    const long long rcap = (long long)kAmgPmax * A.cap_rows;
+    double ovf[2] = {0.0, 0.0};
+    for (int base = tid - lane; base < nc; base += stride) {     // whole warps together
+        const int c = base + lane;
+        int m = 0, nr = 0;
+        double dgc = 0.0;
+        int cols[kAmgRowThread];
+        double vals[kAmgRowThread];
+        bool ok = true;
+        if (c < nc) ok = amg_row_table<CG>(c, A, ro, rp, cl, av, dg, cols, vals, dgc, m, nr);
+        if (!ok) {
+            ovf[0] = 1.0;
+            m = 0;
+            nr = 0;
+        }
+        int pm = m, pr = nr;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int ym = __shfl_up_sync(0xffffffffu, pm, o), yr = __shfl_up_sync(0xffffffffu, pr, o);
+            if (lane >= o) {
+                pm += ym;
+                pr += yr;
+            }
+        }
+        int bm = 0, br = 0;
+        if (lane == 31) {
+            bm = atomicAdd(&A.info->ctr, pm);
+            br = atomicAdd(&A.info->rctr, pr);
+        }
+        bm = __shfl_sync(0xffffffffu, bm, 31);
+        br = __shfl_sync(0xffffffffu, br, 31);
+        const long long pos = (long long)A.cap_nnz - (bm + pm), rpos = rcap - (br + pr);
+        if (c < nc && ok) {
+            if (pos < eo_c || rpos < roff) {
+                ovf[1] = 1.0;
+            } else {
+                for (int u = 0; u < m; u++) {
+                    A.col[pos + u] = cols[u];
+                    A.a64[pos + u] = vals[u];
+                }
+                amg_row_rents<CG>(c, A, ro, rp, cl, A.rent + rpos);
+            }
+            A.diag[ro_c + c] = dgc;
+            A.toff[c] = (int)pos;
+            A.troff[c] = (int)rpos;
+        }
+        if (c < nc) {
             A.cnt[c] = m;
             A.cnt2[c] = nr;
         }
-        if (!allreduce<0, 1>(ovf, w.partials, parity, w.bar, spin, abort_flag, sh, tm)) return kLvlTimeout;
-        warp_rap = ovf[0] != 0.0;
-        ovf[0] = 0.0;
     }
+    if (!allreduce<0, 2>(ovf, w.partials, parity, w.bar, spin, abort_flag, sh, tm)) return kLvlTimeout;
+    const bool warp_rap = ovf[0] != 0.0;
+    bool staged = ovf[1] == 0.0 && !warp_rap;
     if (warp_rap) {
+        double ov[1] = {0.0};
         for (int c = gw; c < nc; c += nwarps) {
             int m = 0, nr = 0;
             const bool ok = amg_coarse_row_warp<false, CG>(c, A, ro, rp, cl, av, dg, msh.rap, wid, lane, nullptr,
@@ -554,11 +615,11 @@ __device__ int amg_level(int l, const Workspace& w, Team tm, int tid, int stride
             if (lane == 0) {
                 A.cnt[c] = m;
                 A.cnt2[c] = nr;
-                if (!ok) ovf[0] = 1.0;
+                if (!ok) ov[0] = 1.0;
             }
         }
-        if (!allreduce<0, 1>(ovf, w.partials, parity, w.bar, spin, abort_flag, sh, tm)) return kLvlTimeout;
-        if (ovf[0] != 0.0) {
+        if (!allreduce<0, 1>(ov, w.partials, parity, w.bar, spin, abort_flag, sh, tm)) return kLvlTimeout;
+        if (ov[0] != 0.0) {
             if (threadIdx.x == 0) as.stop = kAmgStopRowMax;
             return kLvlStop;
         }
@@ -570,20 +631,31 @@ __device__ int amg_level(int l, const Workspace& w, Team tm, int tid, int stride
     int* rr_c = A.rrow + ro_c + (l + 1);
     if (!team_scan(A.cnt, rp_c, nc, nnz_c, w.partials, parity, w.bar, spin, abort_flag, tm, as)) return kLvlTimeout;
     if (!team_scan(A.cnt2, rr_c, nc, rtot, w.partials, parity, w.bar, spin, abort_flag, tm, as)) return kLvlTimeout;
-    const int eo_c = eo + as.nnz[l];
-    const int roff = as.rnz_off[l];
-    if ((long long)eo_c + nnz_c > A.cap_nnz || (long long)roff + rtot > (long long)kAmgPmax * A.cap_rows) {
+    if ((long long)eo_c + nnz_c > A.cap_nnz || (long long)roff + rtot > rcap) {
         if (threadIdx.x == 0) as.stop = kAmgStopNnz;
         return kLvlStop;
     }
+    // the staged rows occupy [cap - nnz_c, cap): usable only if the final places lie below
+    staged = staged && (long long)eo_c + 2ll * nnz_c <= A.cap_nnz && (long long)roff + 2ll * rtot <= rcap;
     if (tid == 0) {
         rp_c[nc] = nnz_c;
         rr_c[nc] = rtot;
     }
     if (!sync()) return kLvlTimeout;
     mark(5);
-    // 9. fill level l+1 and the restriction of level l (the same method as the count)
-    if (warp_rap) {
+    // 9. level l+1 and the restriction of level l in their final places
+    if (staged) {
+        for (int c = tid; c < nc; c += stride) {
+            const int e0 = ldp<CG>(rp_c + c), m = ldp<CG>(A.cnt + c);
+            const int src = ldp<CG>(A.toff + c);
+            for (int u = 0; u < m; u++) {
+                A.col[eo_c + e0 + u] = ldp<CG>(A.col + src + u);
+                A.a64[eo_c + e0 + u] = ldp<CG>(A.a64 + src + u);
+            }
+            const int r0 = ldp<CG>(rr_c + c), nr = ldp<CG>(A.cnt2 + c), rsrc = ldp<CG>(A.troff + c);
+            for (int u = 0; u < nr; u++) A.rent[roff + r0 + u] = ldp<CG>(A.rent + rsrc + u);
+        }
+    } else if (warp_rap) {
         for (int c = gw; c < nc; c += nwarps) {
             int m = 0, nr = 0;
             const int e0 = ldp<CG>(rp_c + c), r0 = ldp<CG>(rr_c + c);
@@ -593,9 +665,17 @@ __device__ int amg_level(int l, const Workspace& w, Team tm, int tid, int stride
     } else {
         for (int c = tid; c < nc; c += stride) {
             int m = 0, nr = 0;
+            double dgc = 0.0;
+            int cols[kAmgRowThread];
+            double vals[kAmgRowThread];
+            amg_row_table<CG>(c, A, ro, rp, cl, av, dg, cols, vals, dgc, m, nr);
             const int e0 = ldp<CG>(rp_c + c), r0 = ldp<CG>(rr_c + c);
-            amg_coarse_row_thread<true, CG>(c, A, ro, rp, cl, av, dg, A.col + eo_c + e0, A.a64 + eo_c + e0,
-                                        A.diag + ro_c + c, A.rent + roff + r0, m, nr);
+            for (int u = 0; u < m; u++) {
+                A.col[eo_c + e0 + u] = cols[u];
+                A.a64[eo_c + e0 + u] = vals[u];
+            }
+            A.diag[ro_c + c] = dgc;
+            amg_row_rents<CG>(c, A, ro, rp, cl, A.rent + roff + r0);
         }
     }
     if (!sync()) return kLvlTimeout;
@@ -637,7 +717,7 @@ __device__ int amg_level(int l, const Workspace& w, Team tm, int tid, int stride
 
 // Builds the hierarchy from the Jacobi-scaled fine system of the workspace (level 0: the
 // unscaled operator recovered as a_ij = -c_ij / (s_i s_j), a_ii = 1 / s_i^2).  Levels with
-// more than kBlockLevelMax rows are coarsened by the whole team, the smaller ones by the
+// more than kAmgBlockMax rows are coarsened by the whole team, the smaller ones by the
 // team's first block alone while the others wait at one barrier.  All blocks call it and
 // leave with the same level table; returns false on a timed-out wait.
 __device__ bool amg_build(const Workspace& w, int nx, int ny, Team team, int tid, int stride, long long spin,
@@ -700,7 +780,7 @@ __device__ bool amg_build(const Workspace& w, int nx, int ny, Team team, int tid
             if (threadIdx.x == 0) as.stop = kAmgStopLevels;
             return 1;
         }
-        return (on_team && team.size > 1 && n <= kBlockLevelMax) ? 2 : 0;
+        return (on_team && team.size > 1 && n <= kAmgBlockMax) ? 2 : 0;
     };
     int l = 0, how = 0;
     while ((how = next(l, true)) == 0) {
@@ -921,17 +1001,67 @@ __device__ void amg_restrict(const AV& F, const AV& C, const int* pc_base, Range
     }
 }
 
-// x_F += P x_C
+// x_F += P x_C (a row's 4 interpolation slots are one 16-byte load each)
 template <bool CG>
 __device__ void amg_prolong(const AV& F, const AV& C, Range rg) {
+    static_assert(kAmgPmax == 4, "one int4 / float4 per interpolation row");
     for (int i = rg.start; i < F.n; i += rg.step) {
+        const int4 pc = reinterpret_cast<const int4*>(F.pc)[i];
+        const float4 pv = reinterpret_cast<const float4*>(F.pv)[i];
         float acc = ldvec<CG>(F.x + i);
-#pragma unroll
-        for (int q = 0; q < kAmgPmax; q++) {
-            const int cc = F.pc[(size_t)kAmgPmax * i + q];
-            if (cc >= 0) acc += F.pv[(size_t)kAmgPmax * i + q] * ldvec<CG>(C.x + cc);
-        }
+        if (pc.x >= 0) acc += pv.x * ldvec<CG>(C.x + pc.x);
+        if (pc.y >= 0) acc += pv.y * ldvec<CG>(C.x + pc.y);
+        if (pc.z >= 0) acc += pv.z * ldvec<CG>(C.x + pc.z);
+        if (pc.w >= 0) acc += pv.w * ldvec<CG>(C.x + pc.w);
         F.x[i] = acc;
+    }
+}
+
+// Level 0 with 4 cells per thread (nx a multiple of 4, team levels): 16-byte loads of the
+// vector, its south and north rows and the coefficients.  MODE 0: out = omega (2 b - omega
+// A^ b) (in = b); 1: out = b - A^ in; 2: out = in + omega (b - A^ in), with the partial sums
+// b.out and b.z_old when rz is given.  c_W of a row's first cell is zero, so the west and
+// east neighbours may cross rows.
+template <int MODE>
+__device__ void amg0_v(const AV& L, const float* in, float* out, float om, Range rg, const float* zold, double* rz,
+                       double* rzo) {
+    const int nx = L.nx, N = L.n, nch = N >> 2;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int ch = rg.start; ch < nch; ch += rg.step) {
+        const int k = ch << 2;
+        const float4 v = __ldcg(reinterpret_cast<const float4*>(in + k));
+        const float vw = k > 0 ? __ldcg(in + k - 1) : 0.f;
+        const float ve = k + 4 < N ? __ldcg(in + k + 4) : 0.f;
+        const float4 vs = k >= nx ? __ldcg(reinterpret_cast<const float4*>(in + k - nx)) : z4;
+        const float4 vn = k + nx < N ? __ldcg(reinterpret_cast<const float4*>(in + k + nx)) : z4;
+        const float4 cw = *reinterpret_cast<const float4*>(L.cW + k);
+        const float4 cs = *reinterpret_cast<const float4*>(L.cS + k);
+        const float4 csn = k + nx < N ? *reinterpret_cast<const float4*>(L.cS + k + nx) : z4;
+        const float cwe = k + 4 < N ? L.cW[k + 4] : 0.f;
+        float a[4];
+        a[0] = v.x - cw.x * vw - cw.y * v.y - cs.x * vs.x - csn.x * vn.x;
+        a[1] = v.y - cw.y * v.x - cw.z * v.z - cs.y * vs.y - csn.y * vn.y;
+        a[2] = v.z - cw.z * v.y - cw.w * v.w - cs.z * vs.z - csn.z * vn.z;
+        a[3] = v.w - cw.w * v.z - cwe * ve - cs.w * vs.w - csn.w * vn.w;
+        const float4 b = MODE == 0 ? v : __ldcg(reinterpret_cast<const float4*>(L.b + k));
+        const float bb[4] = {b.x, b.y, b.z, b.w}, vv[4] = {v.x, v.y, v.z, v.w};
+        float o[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            if constexpr (MODE == 0) o[j] = om * (2.f * bb[j] - om * a[j]);
+            else if constexpr (MODE == 1) o[j] = bb[j] - a[j];
+            else o[j] = vv[j] + om * (bb[j] - a[j]);
+        }
+        *reinterpret_cast<float4*>(out + k) = make_float4(o[0], o[1], o[2], o[3]);
+        if (MODE == 2 && rz) {
+            const float4 zo = __ldcg(reinterpret_cast<const float4*>(zold + k));
+            const float zz[4] = {zo.x, zo.y, zo.z, zo.w};
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                *rz += (double)bb[j] * (double)o[j];
+                *rzo += (double)bb[j] * (double)zz[j];
+            }
+        }
     }
 }
 
@@ -991,21 +1121,24 @@ __device__ bool amg_vcycle(const AMGData& A, AMGShared& as, const float* r0, flo
     const int Lc = nl - 1;
     const bool dense = as.n[Lc] <= kCoarseMax;
     int lg = 0;                                  // levels [0, lg) run on the whole team
-    while (lg < nl - 1 && as.n[lg] > kBlockLevelMax) lg++;
+    while (lg < nl - 1 && as.n[lg] > kAmgBlockMax) lg++;
     // a large coarsest level (coarsening stopped early) is smoothed by the team
-    const bool team_coarse = !dense && as.n[Lc] > kBlockLevelMax;
+    const bool team_coarse = !dense && as.n[Lc] > kAmgBlockMax;
     if (team_coarse) lg = nl - 1;
     const Range tr{tid, stride};
     const Range br{static_cast<int>(threadIdx.x), static_cast<int>(blockDim.x)};
     auto view = [&](int l) { return amg_view(A, as, l, r0, z, cW0, cS0, nx0); };
     auto sync = [&]() { return team_barrier(bar, team, spin, abort_flag); };
 
+    const bool v0 = (nx0 % 4) == 0;
     for (int l = 0; l < lg; l++) {
         const AV F = view(l), C = view(l + 1);
         cyc_mark(as, team, l);
-        amg_pre<true, true>(F, om, tr);
+        if (l == 0 && v0) amg0_v<0>(F, F.b, F.x, om, tr, nullptr, nullptr, nullptr);
+        else amg_pre<true, true>(F, om, tr);
         if (!sync()) return false;
-        amg_resid<true, true>(F, tr);
+        if (l == 0 && v0) amg0_v<1>(F, F.x, F.t, om, tr, nullptr, nullptr, nullptr);
+        else amg_resid<true, true>(F, tr);
         if (!sync()) return false;
         amg_restrict<true>(F, C, A.pc, tr);
         if (!sync()) return false;
@@ -1067,9 +1200,11 @@ __device__ bool amg_vcycle(const AMGData& A, AMGShared& as, const float* r0, flo
         cyc_mark(as, team, l);
         amg_prolong<true>(F, C, tr);
         if (!sync()) return false;
-        amg_sweep<true, true>(F, F.x, F.t, om, tr, nullptr, nullptr, nullptr);
+        if (l == 0 && v0) amg0_v<2>(F, F.x, F.t, om, tr, nullptr, nullptr, nullptr);
+        else amg_sweep<true, true>(F, F.x, F.t, om, tr, nullptr, nullptr, nullptr);
         if (!sync()) return false;
-        amg_sweep<true, true>(F, F.t, F.x, om, tr, zold, l == 0 ? rz : nullptr, rzo);
+        if (l == 0 && v0) amg0_v<2>(F, F.t, F.x, om, tr, zold, rz, rzo);
+        else amg_sweep<true, true>(F, F.t, F.x, om, tr, zold, l == 0 ? rz : nullptr, rzo);
         if (l > 0 && !sync()) return false;
     }
     cyc_mark(as, team, kAmgMaxLevels - 1);

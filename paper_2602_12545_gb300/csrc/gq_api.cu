@@ -240,6 +240,8 @@ void layout(gq_fld_plan* P, Bump& b) {
         a.cf = b.take<int>(N);
         a.cnt = b.take<int>(N + 1);
         a.cnt2 = b.take<int>(N + 1);
+        a.toff = b.take<int>(N);
+        a.troff = b.take<int>(N);
         a.dense = b.take<double>((size_t)gq::kCoarseMax * 2 * gq::kCoarseMax);
         a.inv = b.take<float>((size_t)gq::kCoarseMax * gq::kCoarseMax);
     }

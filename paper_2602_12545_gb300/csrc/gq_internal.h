@@ -94,6 +94,7 @@ struct AMGInfo {
     long long tns[kAmgMaxLevels + 2];  // device clock: start, fine copy done, level l coarsened
     long long bph[8];                  // build time per phase, summed over the levels (ns)
     long long cyc[kAmgMaxLevels];      // time per level over all cycles of the solve; last: the rest
+    int ctr, rctr;                     // tail reservations of the Galerkin product (entries, restriction)
 };
 
 struct AMGData {
@@ -119,6 +120,7 @@ struct AMGData {
     double* wgt;         // [n0] PMIS weights
     signed char *stA, *stB;  // [n0] C/F states
     int *cidx, *cf, *cnt, *cnt2;  // [n0] coarse index, fine index of a coarse row, counts
+    int *toff, *troff;   // [n0] staged places of a coarse row's entries and restriction entries
     double* dense;       // [kCoarseMax][2 kCoarseMax] Gauss-Jordan scratch
     float* inv;          // [kCoarseMax][kCoarseMax] inverse of the coarsest level
 };
