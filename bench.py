@@ -190,7 +190,7 @@ def traffic_from_profile(kernel_tag, src_hash):
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("gq_pcg.cu", "gq_device.cuh", "gq_internal.h"):
+    for name in ("gq_pcg.cu", "gq_mg.cuh", "gq_amg.cuh", "gq_device.cuh", "gq_internal.h"):
         with open(os.path.join(ROOT, "paper_2602_12545_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()

@@ -106,7 +106,11 @@ typedef struct { int side[4]; } gq_bc;
  *               GQ_PRECOND_JACOBI: diagonal (Jacobi) preconditioning only.
  *   mg_omega    Jacobi smoothing weight of the V-cycle, in (0, 1] (0 = default 0.8).
  *   mg_over     coarse-correction factor, in (0, 2) (0 = default 1.5; the AMG cycle
- *               applies no factor). */
+ *               applies no factor).
+ *   mg_block_cells  multigrid levels of at most this many cells are processed by one
+ *               block of the solve (the others wait), larger ones by all blocks with
+ *               grid-wide barriers between passes (0 = default: 4096 for the aggregation
+ *               cycle, 1024 for the algebraic one; >= 0). */
 typedef struct {
     int prec;
     int limiter;
@@ -118,7 +122,7 @@ typedef struct {
     int restart;
     int timing;
     int precond;
-    int reserved0;
+    int mg_block_cells;
     double mg_omega;
     double mg_over;
     int reserved[2];

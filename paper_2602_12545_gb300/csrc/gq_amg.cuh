@@ -32,9 +32,6 @@ namespace gq {
 namespace {
 
 constexpr double kAmgTheta = 0.25;
-// levels of at most this many rows are built and cycled by the team's first block alone
-// (about where one block's sweep costs as much as a team barrier)
-constexpr int kAmgBlockMax = 1024;
 constexpr int kAmgRounds = 40;
 constexpr signed char kStU = 0, kStC = 1, kStF = 2;
 
@@ -717,11 +714,11 @@ __device__ int amg_level(int l, const Workspace& w, Team tm, int tid, int stride
 
 // Builds the hierarchy from the Jacobi-scaled fine system of the workspace (level 0: the
 // unscaled operator recovered as a_ij = -c_ij / (s_i s_j), a_ii = 1 / s_i^2).  Levels with
-// more than kAmgBlockMax rows are coarsened by the whole team, the smaller ones by the
+// more than block_cells rows are coarsened by the whole team, the smaller ones by the
 // team's first block alone while the others wait at one barrier.  All blocks call it and
 // leave with the same level table; returns false on a timed-out wait.
-__device__ bool amg_build(const Workspace& w, int nx, int ny, Team team, int tid, int stride, long long spin,
-                          int* abort_flag, RedShared& sh, MGShared& msh, int& parity) {
+__device__ bool amg_build(const Workspace& w, int nx, int ny, int block_cells, Team team, int tid, int stride,
+                          long long spin, int* abort_flag, RedShared& sh, MGShared& msh, int& parity) {
     const AMGData& A = w.amg;
     AMGShared& as = msh.amg;
     const int n0 = A.n0;
@@ -780,7 +777,7 @@ __device__ bool amg_build(const Workspace& w, int nx, int ny, Team team, int tid
             if (threadIdx.x == 0) as.stop = kAmgStopLevels;
             return 1;
         }
-        return (on_team && team.size > 1 && n <= kAmgBlockMax) ? 2 : 0;
+        return (on_team && team.size > 1 && n <= block_cells) ? 2 : 0;
     };
     int l = 0, how = 0;
     while ((how = next(l, true)) == 0) {
@@ -963,7 +960,20 @@ __device__ __forceinline__ float amg_apply(const AV& L, const float* v, int i, f
         if (i >= nx) ax -= L.cS[i] * ldvec<CG>(v + i - nx);
         if (i + nx < N) ax -= L.cS[i + nx] * ldvec<CG>(v + i + nx);
     } else {
-        for (int e = L.rp[i], ee = L.rp[i + 1]; e < ee; e++) ax += L.a[e] * ldvec<CG>(v + L.col[e]);
+        // four gathers in flight per thread
+        int e = L.rp[i];
+        const int ee = L.rp[i + 1];
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        for (; e + 4 <= ee; e += 4) {
+            const int c0 = L.col[e], c1 = L.col[e + 1], c2 = L.col[e + 2], c3 = L.col[e + 3];
+            const float w0 = L.a[e], w1 = L.a[e + 1], w2 = L.a[e + 2], w3 = L.a[e + 3];
+            a0 += w0 * ldvec<CG>(v + c0);
+            a1 += w1 * ldvec<CG>(v + c1);
+            a2 += w2 * ldvec<CG>(v + c2);
+            a3 += w3 * ldvec<CG>(v + c3);
+        }
+        for (; e < ee; e++) a0 += L.a[e] * ldvec<CG>(v + L.col[e]);
+        ax += (a0 + a1) + (a2 + a3);
     }
     return ax;
 }
@@ -1115,15 +1125,16 @@ __device__ void amg_coarse(const AV& L, const float* inv, bool dense, float om, 
 // z = B r0 on the team; rz, rzo receive this thread's partial sums of r0.z and r0.z_old.
 // Returns false on a timed-out wait.
 __device__ bool amg_vcycle(const AMGData& A, AMGShared& as, const float* r0, float* z, const float* zold,
-                           const float* cW0, const float* cS0, int nx0, float om, Team team, int tid, int stride,
+                           const float* cW0, const float* cS0, int nx0, float om, int block_cells, Team team, int tid,
+                           int stride,
                            unsigned* bar, long long spin, int* abort_flag, double* rz, double* rzo) {
     const int nl = as.nlev;
     const int Lc = nl - 1;
     const bool dense = as.n[Lc] <= kCoarseMax;
     int lg = 0;                                  // levels [0, lg) run on the whole team
-    while (lg < nl - 1 && as.n[lg] > kAmgBlockMax) lg++;
+    while (lg < nl - 1 && as.n[lg] > block_cells) lg++;
     // a large coarsest level (coarsening stopped early) is smoothed by the team
-    const bool team_coarse = !dense && as.n[Lc] > kAmgBlockMax;
+    const bool team_coarse = !dense && as.n[Lc] > block_cells;
     if (team_coarse) lg = nl - 1;
     const Range tr{tid, stride};
     const Range br{static_cast<int>(threadIdx.x), static_cast<int>(blockDim.x)};

@@ -316,6 +316,7 @@ gq_status make_step_params(const gq_fld_plan* P, const double* rho, double* e_g,
     const double omega = opts.mg_omega == 0.0 ? 0.8 : opts.mg_omega;
     const double over = opts.mg_over == 0.0 ? 1.5 : opts.mg_over;
     if (!(omega > 0.0 && omega <= 1.0) || !(over > 0.0 && over < 2.0)) return GQ_ERR_INVALID_ARG;
+    if (opts.mg_block_cells < 0) return GQ_ERR_INVALID_ARG;
 
     StepParams sp{};
     sp.nx = P->nx;
@@ -350,6 +351,8 @@ gq_status make_step_params(const gq_fld_plan* P, const double* rho, double* e_g,
     pp.precond = opts.precond;
     pp.mg_omega = (float)omega;
     pp.mg_over = (float)over;
+    pp.block_cells = opts.mg_block_cells > 0 ? opts.mg_block_cells
+                                             : (opts.precond == GQ_PRECOND_AMG ? 1024 : gq::kBlockLevelMax);
     *sp_out = sp;
     *pp_out = pp;
     if (timing) *timing = opts.timing;

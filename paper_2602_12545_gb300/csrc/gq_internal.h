@@ -47,7 +47,7 @@ struct DeviceGeometry {
 // which the next level is built.
 constexpr int kMaxLevels = 32;
 constexpr int kCoarseMax = 32;       // the coarsest level is solved densely (<= 32 cells)
-constexpr int kBlockLevelMax = 8192; // levels at most this large run inside one block
+constexpr int kBlockLevelMax = 4096; // aggregation levels at most this large run inside one block
 
 struct MGLevel {
     int nx, ny, N;
@@ -176,7 +176,7 @@ struct SolveParams {
     int precond;         // GQ_PRECOND_JACOBI, GQ_PRECOND_MG or GQ_PRECOND_AMG
     float mg_omega;      // Jacobi smoothing weight of the V-cycle
     float mg_over;       // coarse-correction over-relaxation
-    int pad;
+    int block_cells;     // multigrid levels up to this size run in one block
 };
 
 // status of a problem of a batch that no team has solved yet

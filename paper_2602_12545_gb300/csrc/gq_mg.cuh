@@ -12,7 +12,7 @@
 // over < 2, so it is a valid CG preconditioner; it runs in FP32 for both precisions,
 // and the Krylov directions use the Polak-Ribiere beta, which tolerates its rounding.
 //
-// Levels with more than kBlockLevelMax cells are processed by the whole team with team
+// Levels with more than block_cells cells are processed by the whole team with team
 // barriers between sweeps; smaller levels by the team's first block with block
 // barriers, while the other blocks wait at one team barrier.
 #pragma once
@@ -492,11 +492,11 @@ __device__ __forceinline__ Lv level_view(const MGHierarchy& mg, int l, const flo
 // z = B r0 on the team; rz, rzo receive this thread's partial sums of r0.z and r0.zold.
 // Returns false on a timed-out wait.
 __device__ bool vcycle(const MGHierarchy& mg, const float* r0, float* z, const float* zold, float om, float over,
-                       Team team, int tid, int stride, unsigned* bar, long long spin, int* abort_flag, double* rz,
-                       double* rzo) {
+                       int block_cells, Team team, int tid, int stride, unsigned* bar, long long spin,
+                       int* abort_flag, double* rz, double* rzo) {
     const int nl = mg.nlev;
     int lg = 0;                          // levels [0, lg) run on the whole team
-    while (lg < nl - 1 && mg.L[lg].N > kBlockLevelMax) lg++;
+    while (lg < nl - 1 && mg.L[lg].N > block_cells) lg++;
     const Range tr{tid, stride};
     const Range br{static_cast<int>(threadIdx.x), static_cast<int>(blockDim.x)};
     // the fine level uses 4-cell vectors when its rows allow (and its coarse level has an

@@ -235,7 +235,7 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
     float* zc = w.mg.z;
     float* zo = w.mg.zold;
     if constexpr (PC == 2) {
-        if (!amg_build(w, nx, N / nx, team, tid, stride, P.spin_limit, abort_flag, sh, msh, parity)) {
+        if (!amg_build(w, nx, N / nx, P.block_cells, team, tid, stride, P.spin_limit, abort_flag, sh, msh, parity)) {
             if (threadIdx.x == 0) atomicExch(&ctl->status, kErrTimeout);
             return false;
         }
@@ -430,11 +430,11 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
                 double vz[2] = {0.0, 0.0};
                 bool ok;
                 if constexpr (PC == 2)
-                    ok = amg_vcycle(w.amg, msh.amg, r0, zc, zo, w.cW32, w.cS32, nx, P.mg_omega, team, tid, stride,
-                                    w.bar, P.spin_limit, abort_flag, &vz[0], &vz[1]);
+                    ok = amg_vcycle(w.amg, msh.amg, r0, zc, zo, w.cW32, w.cS32, nx, P.mg_omega, P.block_cells, team,
+                                    tid, stride, w.bar, P.spin_limit, abort_flag, &vz[0], &vz[1]);
                 else
-                    ok = vcycle(w.mg, r0, zc, zo, P.mg_omega, P.mg_over, team, tid, stride, w.bar, P.spin_limit,
-                                abort_flag, &vz[0], &vz[1]);
+                    ok = vcycle(w.mg, r0, zc, zo, P.mg_omega, P.mg_over, P.block_cells, team, tid, stride, w.bar,
+                                P.spin_limit, abort_flag, &vz[0], &vz[1]);
                 if (!ok) {
                     timed_out = true;
                     break;

@@ -38,6 +38,7 @@ class SolverOptions:
     precond: int = 2              # 0 Jacobi, 1 aggregation multigrid, 2 algebraic multigrid
     mg_omega: float = 0.0         # 0 = library default
     mg_over: float = 0.0
+    mg_block_cells: int = 0       # 0 = library default
 
     def to_c(self) -> N.SolverOpts:
         o = N.SolverOpts()
@@ -46,6 +47,7 @@ class SolverOptions:
         o.inner_rtol, o.max_refine = float(self.inner_rtol), int(self.max_refine)
         o.spin_limit, o.restart, o.timing = int(self.spin_limit), int(self.restart), int(self.timing)
         o.precond, o.mg_omega, o.mg_over = int(self.precond), float(self.mg_omega), float(self.mg_over)
+        o.mg_block_cells = int(self.mg_block_cells)
         return o
 
 
