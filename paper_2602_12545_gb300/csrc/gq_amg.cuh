@@ -311,11 +311,17 @@ __device__ __forceinline__ bool amg_row_table(int c, const AMGData& A, int ro, c
             const double aik = e < ib ? ldp<CG>(dg + i) : ldp<CG>(av + e);
             if (aik == 0.0) continue;
             const double wa = wi * aik;
+            // the 4 interpolation slots of row k: one 16-byte and two 16-byte loads
+            const int4 pc4 = ldp<CG>(reinterpret_cast<const int4*>(A.pc) + (ro + k));
+            const double2 pv01 = ldp<CG>(reinterpret_cast<const double2*>(A.pv64) + 2 * (size_t)k);
+            const double2 pv23 = ldp<CG>(reinterpret_cast<const double2*>(A.pv64) + 2 * (size_t)k + 1);
+            const int pcs[kAmgPmax] = {pc4.x, pc4.y, pc4.z, pc4.w};
+            const double pvs[kAmgPmax] = {pv01.x, pv01.y, pv23.x, pv23.y};
 #pragma unroll
             for (int q = 0; q < kAmgPmax; q++) {
-                const int cc = ldp<CG>(A.pc + (size_t)kAmgPmax * (ro + k) + q);
+                const int cc = pcs[q];
                 if (cc < 0) continue;
-                const double v = wa * ldp<CG>(A.pv64 + (size_t)kAmgPmax * k + q);
+                const double v = wa * pvs[q];
                 if (cc == c) {
                     dgc += v;
                     continue;
