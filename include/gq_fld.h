@@ -109,8 +109,7 @@ typedef struct { int side[4]; } gq_bc;
  *               applies no factor).
  *   mg_block_cells  multigrid levels of at most this many cells are processed by one
  *               block of the solve (the others wait), larger ones by all blocks with
- *               grid-wide barriers between passes (0 = default: 4096 for the aggregation
- *               cycle, 1024 for the algebraic one; >= 0). */
+ *               grid-wide barriers between passes (0 = default 1024; >= 0). */
 typedef struct {
     int prec;
     int limiter;
@@ -185,7 +184,8 @@ void gq_fld_destroy(gq_fld_plan *plan);
  * hierarchy).  For GQ_PRECOND_AMG: rows and off-diagonal entries of every level as built
  * on the device, why coarsening stopped (1 coarsest small enough, 2 level cap, 3 a level
  * did not shrink, 4 row pool, 5 entry pool, 6 a coarse row too long), and the device time
- * of each part of the build.  For GQ_PRECOND_MG: the fixed 2 x 2 hierarchy's rows.
+ * of each part of the build.  For GQ_PRECOND_MG: the fixed 2 x 2 hierarchy's rows, and the
+ * cycle time with the levels run by one block summed in the slot of the first of them.
  * Synchronises with the device.  GQ_ERR_INVALID_ARG before any step or for Jacobi. */
 typedef struct {
     int precond;
@@ -199,8 +199,11 @@ typedef struct {
     float build_phase_ms[8];    /* AMG: build time per phase summed over the levels (strength,
                                    splitting rounds, numbering, interpolation, product count,
                                    scans, product fill, scaling) */
-    float cycle_ms[24];         /* AMG: time per level summed over the solve's cycles; the last
-                                   entry is the time outside the cycle (Krylov updates) */
+    float cycle_ms[24];         /* multigrid: time per level summed over the solve's cycles
+                                   (levels 0..19); [20] the direction pass and its reduction,
+                                   [21] the update pass, its reduction and the stop test,
+                                   [22] the FP64 residual evaluations, [23] the reduction after
+                                   the cycle (device clock of the first block) */
 } gq_precond_info;
 
 gq_status gq_fld_precond_info(const gq_fld_plan *plan, gq_precond_info *out);

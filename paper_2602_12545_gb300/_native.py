@@ -76,7 +76,10 @@ class PrecondInfo(ctypes.Structure):
                 "rows": list(self.rows[:n]), "entries": list(self.entries[:n]),
                 "build_ms": list(self.build_ms[:max(n - 1, 0)]), "fine_copy_ms": self.fine_copy_ms,
                 "coarsest_ms": self.coarsest_ms, "build_phase_ms": list(self.build_phase_ms),
-                "cycle_ms": list(self.cycle_ms[:n]), "outside_cycle_ms": self.cycle_ms[23]}
+                "cycle_ms": list(self.cycle_ms[:min(n, 20)]), "direction_ms": self.cycle_ms[20],
+                "update_ms": self.cycle_ms[21], "refine_ms": self.cycle_ms[22],
+                "after_cycle_ms": self.cycle_ms[23],
+                "outside_cycle_ms": sum(self.cycle_ms[20:24])}
 
 
 class BatchItem(ctypes.Structure):

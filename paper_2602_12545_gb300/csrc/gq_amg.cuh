@@ -877,25 +877,11 @@ __device__ bool amg_build(const Workspace& w, int nx, int ny, int block_cells, T
             as.rnz_off[k] = __ldcg(&I->rnz_off[k]);
         }
     }
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < kAmgMaxLevels; k++) as.cyc[k] = 0;
-        as.tcyc = global_ns();
-        as.ccur = kAmgMaxLevels - 1;
-    }
+    cyc_reset(as);
     __syncthreads();
     return true;
 }
 
-// cycle timing: the time since the last mark goes to the slot then current (block 0's
-// first thread only; the last slot collects the time outside the cycle)
-__device__ __forceinline__ void cyc_mark(AMGShared& as, Team team, int slot) {
-    if (team.rank == 0 && threadIdx.x == 0) {
-        const long long t = global_ns();
-        as.cyc[as.ccur] += t - as.tcyc;
-        as.tcyc = t;
-        as.ccur = slot;
-    }
-}
 
 // writes the cycle timing of the solve to the device info block
 __device__ void amg_cycle_report(const AMGData& A, AMGShared& as, Team team) {

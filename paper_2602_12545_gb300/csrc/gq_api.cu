@@ -351,8 +351,7 @@ gq_status make_step_params(const gq_fld_plan* P, const double* rho, double* e_g,
     pp.precond = opts.precond;
     pp.mg_omega = (float)omega;
     pp.mg_over = (float)over;
-    pp.block_cells = opts.mg_block_cells > 0 ? opts.mg_block_cells
-                                             : (opts.precond == GQ_PRECOND_AMG ? 1024 : gq::kBlockLevelMax);
+    pp.block_cells = opts.mg_block_cells > 0 ? opts.mg_block_cells : gq::kBlockLevelMax;
     *sp_out = sp;
     *pp_out = pp;
     if (timing) *timing = opts.timing;
@@ -504,18 +503,7 @@ gq_status gq_fld_precond_info(const gq_fld_plan* P, gq_precond_info* out) {
     if (!P || !out) return GQ_ERR_INVALID_ARG;
     std::memset(out, 0, sizeof(*out));
     out->precond = P->last_precond;
-    if (P->last_precond == GQ_PRECOND_MG) {
-        const gq::MGHierarchy& mg = P->ws.mg;
-        out->levels = mg.nlev;
-        out->stop_reason = 1;
-        for (int l = 0; l < mg.nlev && l < 24; l++) {
-            const gq::MGLevel& L = mg.L[l];
-            out->rows[l] = L.N;
-            out->entries[l] = 2 * ((L.nx - 1) * L.ny + L.nx * (L.ny - 1));
-        }
-        return GQ_OK;
-    }
-    if (P->last_precond != GQ_PRECOND_AMG) return GQ_ERR_INVALID_ARG;
+    if (P->last_precond != GQ_PRECOND_AMG && P->last_precond != GQ_PRECOND_MG) return GQ_ERR_INVALID_ARG;
     gq::AMGInfo I{};
     int cur = -1;
     if (cudaGetDevice(&cur) != cudaSuccess) return GQ_ERR_CUDA;
@@ -525,6 +513,20 @@ gq_status gq_fld_precond_info(const gq_fld_plan* P, gq_precond_info* out) {
     if (e != cudaSuccess) {
         cudaGetLastError();
         return GQ_ERR_CUDA;
+    }
+    for (int k = 0; k < gq::kAmgMaxLevels && k < 24; k++) out->cycle_ms[k] = (float)(I.cyc[k] * 1e-6);
+    if (P->last_precond == GQ_PRECOND_MG) {
+        // the fixed 2 x 2 hierarchy; its cycle time: team levels one by one, the levels
+        // run by block 0 together in the slot of the first of them
+        const gq::MGHierarchy& mg = P->ws.mg;
+        out->levels = mg.nlev;
+        out->stop_reason = 1;
+        for (int l = 0; l < mg.nlev && l < 24; l++) {
+            const gq::MGLevel& L = mg.L[l];
+            out->rows[l] = L.N;
+            out->entries[l] = 2 * ((L.nx - 1) * L.ny + L.nx * (L.ny - 1));
+        }
+        return GQ_OK;
     }
     const int nl = std::min(std::max(I.nlev, 0), std::min(gq::kAmgMaxLevels, 24));
     out->levels = nl;
@@ -539,7 +541,6 @@ gq_status gq_fld_precond_info(const gq_fld_plan* P, gq_precond_info* out) {
         out->coarsest_ms = (float)((I.tns[nl + 1] - I.tns[nl]) * 1e-6);
     }
     for (int k = 0; k < 8; k++) out->build_phase_ms[k] = (float)(I.bph[k] * 1e-6);
-    for (int k = 0; k < gq::kAmgMaxLevels && k < 24; k++) out->cycle_ms[k] = (float)(I.cyc[k] * 1e-6);
     return GQ_OK;
 }
 

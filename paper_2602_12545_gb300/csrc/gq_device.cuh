@@ -60,7 +60,8 @@ __device__ __forceinline__ double warp_reduce(double v) {
 // the word's top bit flips exactly when the last block arrives and its low bits return
 // to where they were (no reset between barriers).  The arrival is an acquire-release
 // atomic and the poll an acquire load, so writes before the barrier are visible after
-// it.  A block that polls more than spin_limit times (or sees *abort_flag set) gives up,
+// it.  The abort flag is read every 64th poll.  A block that polls more than spin_limit
+// times (or sees *abort_flag set) gives up,
 // sets *abort_flag and returns false; every caller must then leave the kernel.  No wait
 // in this library is unbounded.
 // ---------------------------------------------------------------------------
@@ -102,7 +103,8 @@ __device__ __forceinline__ bool team_barrier(unsigned* bar, Team team, long long
         const unsigned old = atom_add_acq_rel_gpu(bar, inc);
         long long n = 0;
         while (((ld_acquire_gpu(bar) ^ old) & 0x80000000u) == 0u) {
-            if (++n > spin_limit || ld_volatile_int(abort_flag)) {
+            ++n;
+            if (n > spin_limit || ((n & 63) == 0 && ld_volatile_int(abort_flag))) {
                 atomicExch(abort_flag, 1);
                 ok = 0;
                 break;

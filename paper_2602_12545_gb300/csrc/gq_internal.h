@@ -47,7 +47,7 @@ struct DeviceGeometry {
 // which the next level is built.
 constexpr int kMaxLevels = 32;
 constexpr int kCoarseMax = 32;       // the coarsest level is solved densely (<= 32 cells)
-constexpr int kBlockLevelMax = 4096; // aggregation levels at most this large run inside one block
+constexpr int kBlockLevelMax = 1024; // multigrid levels at most this large run inside one block
 
 struct MGLevel {
     int nx, ny, N;

@@ -48,6 +48,26 @@ struct RapShared {
     int tcol[kSolveThreads / 32][kAmgRowMax];
 };
 
+// cycle timing: the time since the last mark goes to the slot then current (block 0's
+// first thread only; the last slot collects the time outside the cycle)
+__device__ __forceinline__ void cyc_mark(AMGShared& as, Team team, int slot) {
+    if (team.rank == 0 && threadIdx.x == 0) {
+        const long long t = global_ns();
+        as.cyc[as.ccur] += t - as.tcyc;
+        as.tcyc = t;
+        as.ccur = slot;
+    }
+}
+
+// starts the cycle timing of a solve
+__device__ __forceinline__ void cyc_reset(AMGShared& as) {
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < kAmgMaxLevels; k++) as.cyc[k] = 0;
+        as.tcyc = global_ns();
+        as.ccur = kAmgMaxLevels - 1;
+    }
+}
+
 struct MGShared {
     union {                                 // never in use at the same time
         GJShared gj;
@@ -491,8 +511,8 @@ __device__ __forceinline__ Lv level_view(const MGHierarchy& mg, int l, const flo
 
 // z = B r0 on the team; rz, rzo receive this thread's partial sums of r0.z and r0.zold.
 // Returns false on a timed-out wait.
-__device__ bool vcycle(const MGHierarchy& mg, const float* r0, float* z, const float* zold, float om, float over,
-                       int block_cells, Team team, int tid, int stride, unsigned* bar, long long spin,
+__device__ bool vcycle(const MGHierarchy& mg, AMGShared& as, const float* r0, float* z, const float* zold, float om,
+                       float over, int block_cells, Team team, int tid, int stride, unsigned* bar, long long spin,
                        int* abort_flag, double* rz, double* rzo) {
     const int nl = mg.nlev;
     int lg = 0;                          // levels [0, lg) run on the whole team
@@ -504,6 +524,7 @@ __device__ bool vcycle(const MGHierarchy& mg, const float* r0, float* z, const f
     const bool v0 = lg > 0 && (mg.L[0].nx % 4) == 0 && nl > 1;
     for (int l = 0; l < lg; l++) {
         const Lv F = level_view(mg, l, r0, z), C = level_view(mg, l + 1, r0, z);
+        cyc_mark(as, team, l);
         if (l == 0 && v0) cyc0_presmooth_v(F, om, Range{tid, stride});
         else cyc_presmooth<true>(F, om, tr, true);
         if (!team_barrier(bar, team, spin, abort_flag)) return false;
@@ -512,6 +533,7 @@ __device__ bool vcycle(const MGHierarchy& mg, const float* r0, float* z, const f
         if (!team_barrier(bar, team, spin, abort_flag)) return false;
     }
     if (team.rank == 0) {
+        cyc_mark(as, team, lg);      // all block levels together
         for (int l = lg; l + 1 < nl; l++) {
             const Lv F = level_view(mg, l, r0, z), C = level_view(mg, l + 1, r0, z);
             // the first block level's right-hand side comes from the team (or is r0)
@@ -541,6 +563,7 @@ __device__ bool vcycle(const MGHierarchy& mg, const float* r0, float* z, const f
     if (!team_barrier(bar, team, spin, abort_flag)) return false;
     for (int l = lg - 1; l >= 0; l--) {
         const Lv F = level_view(mg, l, r0, z), C = level_view(mg, l + 1, r0, z);
+        cyc_mark(as, team, l);
         if (l == 0 && v0) cyc0_prolong_smooth_v(F, C, om, over, tr);
         else cyc_prolong_smooth<true>(F, C, om, over, tr);
         if (!team_barrier(bar, team, spin, abort_flag)) return false;
@@ -548,6 +571,7 @@ __device__ bool vcycle(const MGHierarchy& mg, const float* r0, float* z, const f
         else cyc_postsmooth<true>(F, om, tr, zold, l == 0 ? rz : nullptr, rzo);
         if (l > 0 && !team_barrier(bar, team, spin, abort_flag)) return false;
     }
+    cyc_mark(as, team, kAmgMaxLevels - 1);
     return true;
 }
 

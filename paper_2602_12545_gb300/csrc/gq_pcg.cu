@@ -240,6 +240,7 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
             return false;
         }
     } else if constexpr (MG) {
+        cyc_reset(msh.amg);
         if (!mg_build(w, team, tid, stride, P.spin_limit, abort_flag, msh)) {
             if (threadIdx.x == 0) atomicExch(&ctl->status, kErrTimeout);
             return false;
@@ -433,8 +434,8 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
                     ok = amg_vcycle(w.amg, msh.amg, r0, zc, zo, w.cW32, w.cS32, nx, P.mg_omega, P.block_cells, team,
                                     tid, stride, w.bar, P.spin_limit, abort_flag, &vz[0], &vz[1]);
                 else
-                    ok = vcycle(w.mg, r0, zc, zo, P.mg_omega, P.mg_over, P.block_cells, team, tid, stride, w.bar,
-                                P.spin_limit, abort_flag, &vz[0], &vz[1]);
+                    ok = vcycle(w.mg, msh.amg, r0, zc, zo, P.mg_omega, P.mg_over, P.block_cells, team, tid, stride,
+                                w.bar, P.spin_limit, abort_flag, &vz[0], &vz[1]);
                 if (!ok) {
                     timed_out = true;
                     break;
@@ -458,6 +459,7 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
             }
             if (!degenerate) {
                 // ---- S: p = r + beta p_old ; q = A^ p ; p.q ------------------------------
+                if constexpr (MG) cyc_mark(msh.amg, team, kAmgMaxLevels - 4);
                 const R* __restrict__ pold = pb[cur];
                 R* __restrict__ pnew = pb[cur ^ 1];
                 const R rb = static_cast<R>(beta);
@@ -575,6 +577,7 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
                     from64 = false;
 
                     // ---- U: x += alpha p ; r -= alpha q ; r.r --------------------------------
+                    if constexpr (MG) cyc_mark(msh.amg, team, kAmgMaxLevels - 3);
                     double v2[2] = {0.0, 0.0};
                     const R ra = static_cast<R>(alpha);
                     for (int c = tid; c < nchunk; c += stride) {
@@ -623,12 +626,13 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
                 }
             }
 
+            if constexpr (MG) cyc_mark(msh.amg, team, kAmgMaxLevels - 2);
             if (!refine()) break;
         }
     }
 
 done:
-    if constexpr (PC == 2) {
+    if constexpr (PC != 0) {
         if (!timed_out) amg_cycle_report(w.amg, msh.amg, team);
     }
     if (timed_out) {
