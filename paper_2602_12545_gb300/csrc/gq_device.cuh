@@ -82,6 +82,24 @@ __device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned* p, unsigned v
     return old;
 }
 
+// |a / b| to about two FP32 ulps, for any FP64 a and b: the two significands (in [1, 2))
+// are divided in FP32 and the exponent difference is applied in FP64 as two exact
+// power-of-two factors, so quotients far outside the FP32 range are still right.  Zero,
+// subnormal, infinite and NaN operands take the FP64 division.  Used for the cell-wise
+// stop criterion and the reported 2-norm, where the FP64 division (slow on this part)
+// buys nothing.
+__device__ __forceinline__ double abs_ratio_approx(double a, double b) {
+    const long long ab = __double_as_longlong(a), bb = __double_as_longlong(b);
+    const int ea = (int)((ab >> 52) & 0x7ff), eb = (int)((bb >> 52) & 0x7ff);
+    if (ea == 0 || eb == 0 || ea == 0x7ff || eb == 0x7ff) return fabs(a / b);
+    const double ma = __longlong_as_double((ab & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
+    const double mb = __longlong_as_double((bb & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
+    const double q = (double)__fdividef((float)ma, (float)mb);
+    const int d = ea - eb, d1 = d / 2, d2 = d - d1;       // each within [-1023, 1023]
+    return q * __longlong_as_double((long long)(d1 + 1023) << 52) *
+           __longlong_as_double((long long)(d2 + 1023) << 52);
+}
+
 // device clock in nanoseconds (for the timings reported in gq_step_info)
 __device__ __forceinline__ long long global_ns() {
     unsigned long long t;

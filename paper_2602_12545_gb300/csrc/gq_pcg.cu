@@ -289,14 +289,14 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
                 if (hs) ax -= cs[i] * ys[i];
                 if (hn) ax -= csn[i] * yn[i];
                 rk[i] = bk[i] - ax;
-                const double ru = rk[i] / sk[i];
+                const double ru = abs_ratio_approx(rk[i], sk[i]);
                 tr[0] += rk[i] * rk[i];
                 tr[1] += ru * ru;
                 if (first) {
-                    const double bu = bk[i] / sk[i];
+                    const double bu = abs_ratio_approx(bk[i], sk[i]);
                     tr[2] += bu * bu;
                 }
-                tr[3] = nanmax(tr[3], fabs(rk[i] / yc[i]));
+                tr[3] = nanmax(tr[3], abs_ratio_approx(rk[i], yc[i]));
                 tr[4] = nanmax(tr[4], fabs(rk[i]));
             }
             st64<W>(r64 + k, rk);
@@ -595,7 +595,7 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
                             // recursive stop estimate in FP32 (FP64 division is slow on this part;
                             // the decisive test uses the exact FP64 residual)
                             if constexpr (!MIXED)
-                                v2[1] = nanmax(v2[1], (double)__fdividef((float)fabs(rk[i]), (float)fabs(xk[i])));
+                                v2[1] = nanmax(v2[1], abs_ratio_approx(rk[i], xk[i]));
                         }
                         stv<R, W>(r + k, rk);
                         stv<R, W>(d + k, xk);
