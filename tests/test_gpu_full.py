@@ -1,6 +1,7 @@
 """Full-size parity: the 1024 x 1024 geometric Cartesian workload (FP64 path, 1e-10) and the
 2048 x 1024 spherical-polar workload (mixed path, 1e-8) against the oracle's own CG solve,
-every cell compared, in the launch configuration the benchmark times.  The oracle solves
+every cell compared, in the launch configuration the benchmark times (and, for the
+spherical workload, also with the default algebraic preconditioner).  The oracle solves
 take a minute or two of host time each."""
 import numpy as np
 import pytest
@@ -21,10 +22,10 @@ def fld():
     return F
 
 
-def run(F, P, prec, rtol):
+def run(F, P, prec, rtol, **kw):
     plan = F.FLDPlan.for_problem(P)
     rho, e_g, E, T = F.device_fields(P)
-    info = F.step_problem(plan, P, rho, e_g, E, T, prec=prec, rtol=rtol)
+    info = F.step_problem(plan, P, rho, e_g, E, T, prec=prec, rtol=rtol, **kw)
     out = {"E_r": E.cpu().numpy(), "T_g": T.cpu().numpy(), "e_g": e_g.cpu().numpy(), "info": info}
     plan.close()
     return out
@@ -45,14 +46,21 @@ def test_config1_fp64_full(fld, orc):
     assert max(err.values()) <= 1e-10, err
 
 
-def test_config2_mixed_full(fld, orc):
+@pytest.fixture(scope="module")
+def config2_ref(orc):
     P = W.config2()
     ref = orc.step(P, "cg", tol=1e-15)
     assert ref["cell_residual"] < 1e-12
-    out = run(fld, P, W.PREC_MIXED, 1e-11)
+    return P, ref
+
+
+@pytest.mark.parametrize("precond", [1, 2])     # 1: the benchmark's aggregation cycle, 2: the default
+def test_config2_mixed_full(fld, config2_ref, precond):
+    P, ref = config2_ref
+    out = run(fld, P, W.PREC_MIXED, 1e-11, precond=precond)
     assert out["info"]["status"] == 0, out["info"]
     err = errors(out, ref)
-    print("config2 mixed", err, out["info"]["iterations"], out["info"]["refinements"])
+    print("config2 mixed", precond, err, out["info"]["iterations"], out["info"]["refinements"])
     assert max(err.values()) <= 1e-8, err
     e0, e1 = out["info"]["energy_before"], out["info"]["energy_after"]
     assert e1 < e0      # Milne outer boundary: energy leaves the grid
