@@ -85,8 +85,9 @@ typedef struct { int side[4]; } gq_bc;
  *   inner_rtol  mixed only: FP32 residual drop that triggers an FP64 refinement, in (0, 1).
  *   max_refine  cap on FP64 residual evaluations after the first (> 0).  Independently,
  *               the solve ends with GQ_ERR_NOT_CONVERGED when six consecutive FP64
- *               residuals fail to improve the best one by 10% (rtol below the FP64
- *               rounding floor of the cell-wise residual).
+ *               residuals, spanning at least 32 Krylov iterations, fail to improve the
+ *               best one by 10% (rtol below the FP64 rounding floor of the cell-wise
+ *               residual).
  *   spin_limit  cap on the polling iterations of any inter-block wait (0 = default, about
  *               a second); exceeding it ends the solve with GQ_ERR_TIMEOUT.
  *   restart     mixed only: 1 restarts the Krylov space at every refinement (classical

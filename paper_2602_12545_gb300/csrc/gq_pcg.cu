@@ -26,8 +26,8 @@
 // search direction is kept (reliable update) unless `restart` is set.  The FP32 residual
 // is carried with a fixed power-of-two scale so that its entries stay O(1).
 // Both paths end with GQ_ERR_NOT_CONVERGED (best iterate kept) when the true residual
-// has not improved by 10% in 6 consecutive checks: the FP64 rounding floor of the
-// cell-wise criterion lies above rtol.
+// has not improved by 10% in 6 consecutive checks spanning at least 32 iterations: the
+// FP64 rounding floor of the cell-wise criterion lies above rtol.
 #include <type_traits>
 
 #include "gq_device.cuh"
@@ -39,6 +39,7 @@ namespace {
 
 constexpr double kStallGain = 0.9;   // a true residual must improve by 10% ...
 constexpr int kStallChecks = 6;      // ... within this many consecutive checks
+constexpr int kStallIters = 32;      // ... spanning at least this many Krylov iterations
 
 struct RedShared {
     double warp[kSolveThreads / 32][kSlots];
@@ -331,6 +332,7 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
         // disagrees; both paths: stop once the true residual stalls (FP64 rounding floor)
         double rec_target = P.rtol;
         double best = crit;
+        int it_best = 0;
         int stall = 0;
         // multigrid: FP32 copy of the (scaled) FP64 residual for the V-cycle
         bool first = true;
@@ -393,11 +395,12 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
             if (crit <= P.rtol) { status = kOk; return false; }
             if (crit < kStallGain * best) {
                 best = crit;
+                it_best = it;
                 stall = 0;
             } else {
                 stall++;
             }
-            if (it >= P.max_iter || nref >= P.max_refine || stall >= kStallChecks) {
+            if (it >= P.max_iter || nref >= P.max_refine || (stall >= kStallChecks && it - it_best >= kStallIters)) {
                 status = kErrNotConverged;
                 return false;
             }
