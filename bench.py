@@ -218,6 +218,38 @@ def oracle_sample(P, iters_needed, cg_iters=60):
 
 
 # ---------------------------------------------------------------------------
+# ranks: one process per GPU, independent replicas (no data-path collective)
+# ---------------------------------------------------------------------------
+
+def dist_init(world, local):
+    """Joins the process group of a torchrun launch: NCCL on GPUs, gloo without one."""
+    import torch
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        if torch.cuda.is_available():
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group("gloo")
+
+
+def job_ms(local_ms, world):
+    """The slowest rank's timed total: a barrier, then a max over the ranks."""
+    if world <= 1:
+        return local_ms
+    import torch
+    import torch.distributed as dist
+    dist.barrier()
+    t = torch.tensor([local_ms], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, ms):
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return world * units_per_rank / (ms / 1e3)
+
+
+# ---------------------------------------------------------------------------
 # our implementation
 # ---------------------------------------------------------------------------
 
@@ -231,8 +263,7 @@ def run_ours(args):
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dist_init(world, local)
 
     def barrier():
         if world > 1:
@@ -286,13 +317,9 @@ def run_ours(args):
     err_E = float(((E - E_ref).abs() / E_ref.abs()).max())
     err_T = float(((T - T_ref).abs() / T_ref.abs()).max())
 
-    total_ms = sum(i["ms"] for i in infos)
-    if world > 1:
-        tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = job_ms(sum(i["ms"] for i in infos), world)
     N = P.ncells
-    value = world * N * args.steps / (total_ms / 1e3)
+    value = job_value(N * args.steps, world, total_ms)
     lat = sorted(i["ms"] for i in infos)
     p50 = statistics.median(lat)
     p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
@@ -423,6 +450,7 @@ def run_batched(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dist_init(world, int(os.environ.get("LOCAL_RANK", "0")))
     probs = W.config3(args.problems)
     plans = [F.FLDPlan.for_problem(P) for P in probs]
     pristine = [F.device_fields(P) for P in probs]
@@ -453,7 +481,7 @@ def run_batched(args):
         rc, infos = B.step(probs, fields, opts, check=False)
         ms.append(B.last_ms)
     ck = clocks.stop()
-    total_ms = sum(ms)
+    total_ms = job_ms(sum(ms), world)
     cells = sum(P.ncells for P in probs)
     # accuracy on a few members against their own tightly solved FP64 step
     errs = []
@@ -464,7 +492,7 @@ def run_batched(args):
         F.step_problem(plans[p], P, r0, e1, E1, T1, prec=0, rtol=1e-13, check=False, precond=args.precond)
         errs.append(float(((fields[p][2] - E1).abs() / E1.abs()).max()))
     its = [i["iterations"] for i in infos]
-    line = _batch_line(args, world, world * cells * args.steps / (total_ms / 1e3), total_ms, infos, {
+    line = _batch_line(args, world, job_value(cells * args.steps, world, total_ms), total_ms, infos, {
         "config": {"workload": f"c3_batch{len(probs)}_mixed", "problems": len(probs), "cells": cells,
                    "sides": "nx, ny log-uniform in [32, 512], Cartesian and spherical-polar alternating",
                    "rtol": probs[0].rtol, "preconditioner": PRECOND_NAMES[args.precond],
@@ -491,8 +519,10 @@ def run_serving(args):
     from paper_2602_12545_gb300 import fld as F
     from paper_2602_12545_gb300 import serve as S
     from paper_2602_12545_gb300 import workloads as W
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dist_init(world, int(os.environ.get("LOCAL_RANK", "0")))
     trace = W.config4_trace(args.requests, rate_per_s=args.rate)
     opts = F.SolverOptions(prec=1, limiter=0, rtol=1e-8, precond=args.precond)
     budget = int(args.budget_gb * (1 << 30))
@@ -518,8 +548,10 @@ def run_serving(args):
         cells_seq += P.ncells * req.n_steps
         plan.close()
     done = out.pop("completed")
+    # every rank serves the same trace on its own GPU: the job's time is the slowest makespan
+    mk_ms = job_ms(1e3 * out["makespan_s"], world)
     line = {
-        "metric": METRIC, "value": out["throughput_cell_updates_per_s"], "unit": UNIT, "n_gpus": 1,
+        "metric": METRIC, "value": job_value(out["cell_steps"], world, mk_ms), "unit": UNIT, "n_gpus": world,
         "steps": args.requests, "warmup": len(warm), "ms_per_step": 1e3 * out["makespan_s"] / max(1, len(done)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": f"c4_serving_{args.requests}req_{int(args.rate)}per_s", "requests": args.requests,
