@@ -166,6 +166,7 @@ void layout(gq_fld_plan* P, Bump& b) {
     w.p32[0] = b.take<float>(N);
     w.p32[1] = b.take<float>(N);
     w.q32 = b.take<float>(N);
+    w.r32b = b.take<float>(N);
     // multigrid hierarchy: level l has ceil(nx / 2^l) x ceil(ny / 2^l) cells; coarsen until
     // the level has at most kCoarseMax cells
     {

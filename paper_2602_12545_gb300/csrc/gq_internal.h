@@ -138,6 +138,7 @@ struct Workspace {
     double *y, *r64, *p64[2], *q64;
     // solve (FP32 inner path)
     float *cW32, *cS32, *d32, *r32, *p32[2], *q32;
+    float *r32b;     // second FP32 residual (the fused update writes the new one beside the old)
     // reductions, barrier, control
     MGHierarchy mg;
     AMGData amg;

@@ -406,6 +406,43 @@ __device__ void cyc0_presmooth_v(const Lv& L, float om, Range rg) {
     }
 }
 
+// The Krylov update r' = r - alpha q, d += alpha p fused with the next cycle's level-0
+// pre-smoothing (two Jacobi sweeps from zero on r'): r' is formed on the chunk and its
+// neighbours from r and q, so no barrier separates the two.  r' goes to rnew (r stays
+// intact for the neighbours of other threads); rr receives this thread's sum of r'^2.
+__device__ void cyc0_update_presmooth_v(const Lv& L, const float* rold, float* rnew, const float* q, const float* p,
+                                        float* d, float alpha, float om, Range rg, double* rr) {
+    const int nx = L.nx, N = L.N, nchunk = N / 4;
+    for (int ch = rg.start; ch < nchunk; ch += rg.step) {
+        const int k = 4 * ch;
+        F4 c, s, n, qc, qs, qn;
+        float w, e, qw, qe;
+        nb4(rold, k, nx, N, c, s, n, w, e);
+        nb4(q, k, nx, N, qc, qs, qn, qw, qe);
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            c.v[i] = c.v[i] - alpha * qc.v[i];
+            s.v[i] = s.v[i] - alpha * qs.v[i];
+            n.v[i] = n.v[i] - alpha * qn.v[i];
+        }
+        w = w - alpha * qw;
+        e = e - alpha * qe;
+        const F4 a = apply4(c, s, n, w, e, L.cW, L.cS, k, nx, N);
+        F4 x;
+        F4 dk = ld4(d + k);
+        const F4 pk = ld4(p + k);
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            x.v[i] = om * (2.f * c.v[i] - om * a.v[i]);
+            dk.v[i] = dk.v[i] + alpha * pk.v[i];
+            *rr += static_cast<double>(c.v[i]) * static_cast<double>(c.v[i]);
+        }
+        st4(L.xa + k, x);
+        st4(rnew + k, c);
+        st4(d + k, dk);
+    }
+}
+
 __device__ void cyc0_postsmooth_v(const Lv& L, float om, Range rg, const float* zold, double* rz, double* rzo) {
     const int nx = L.nx, N = L.N, nchunk = N / 4;
     for (int q = rg.start; q < nchunk; q += rg.step) {
@@ -512,8 +549,8 @@ __device__ __forceinline__ Lv level_view(const MGHierarchy& mg, int l, const flo
 // z = B r0 on the team; rz, rzo receive this thread's partial sums of r0.z and r0.zold.
 // Returns false on a timed-out wait.
 __device__ bool vcycle(const MGHierarchy& mg, AMGShared& as, const float* r0, float* z, const float* zold, float om,
-                       float over, int block_cells, Team team, int tid, int stride, unsigned* bar, long long spin,
-                       int* abort_flag, double* rz, double* rzo) {
+                       float over, int block_cells, bool pre0_done, Team team, int tid, int stride, unsigned* bar,
+                       long long spin, int* abort_flag, double* rz, double* rzo) {
     const int nl = mg.nlev;
     int lg = 0;                          // levels [0, lg) run on the whole team
     while (lg < nl - 1 && mg.L[lg].N > block_cells) lg++;
@@ -525,9 +562,13 @@ __device__ bool vcycle(const MGHierarchy& mg, AMGShared& as, const float* r0, fl
     for (int l = 0; l < lg; l++) {
         const Lv F = level_view(mg, l, r0, z), C = level_view(mg, l + 1, r0, z);
         cyc_mark(as, team, l);
-        if (l == 0 && v0) cyc0_presmooth_v(F, om, Range{tid, stride});
-        else cyc_presmooth<true>(F, om, tr, true);
-        if (!team_barrier(bar, team, spin, abort_flag)) return false;
+        // level 0's pre-smoothing may already be done by the fused Krylov update (whose
+        // reduction was the barrier)
+        if (!(l == 0 && v0 && pre0_done)) {
+            if (l == 0 && v0) cyc0_presmooth_v(F, om, Range{tid, stride});
+            else cyc_presmooth<true>(F, om, tr, true);
+            if (!team_barrier(bar, team, spin, abort_flag)) return false;
+        }
         if (l == 0 && v0) cyc0_restrict_v(F, C, tr);
         else cyc_restrict<true>(F, C, tr);
         if (!team_barrier(bar, team, spin, abort_flag)) return false;

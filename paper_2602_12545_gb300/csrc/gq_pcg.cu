@@ -233,6 +233,13 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
     // multigrid: the rest of the hierarchy, the FP32 level-0 right-hand side and the two
     // preconditioned-residual buffers
     float* r0 = MIXED ? w.r32 : w.mg.r32;
+    // mixed aggregation-multigrid path with a vectorised level 0 on the team: the Krylov
+    // update is fused with the next cycle's first level-0 sweep, the residual alternating
+    // between two buffers
+    float* rbuf[2] = {w.r32, w.r32b};
+    int rsel = 0;
+    const bool fuse = MIXED && PC == 1 && W == 4 && w.mg.nlev > 1 && w.mg.L[0].N > P.block_cells;
+    bool pre0_done = false;
     float* zc = w.mg.z;
     float* zo = w.mg.zold;
     if constexpr (PC == 2) {
@@ -437,8 +444,9 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
                     ok = amg_vcycle(w.amg, msh.amg, r0, zc, zo, w.cW32, w.cS32, nx, P.mg_omega, P.block_cells, team,
                                     tid, stride, w.bar, P.spin_limit, abort_flag, &vz[0], &vz[1]);
                 else
-                    ok = vcycle(w.mg, msh.amg, r0, zc, zo, P.mg_omega, P.mg_over, P.block_cells, team, tid, stride,
-                                w.bar, P.spin_limit, abort_flag, &vz[0], &vz[1]);
+                    ok = vcycle(w.mg, msh.amg, r0, zc, zo, P.mg_omega, P.mg_over, P.block_cells, pre0_done, team, tid,
+                                stride, w.bar, P.spin_limit, abort_flag, &vz[0], &vz[1]);
+                pre0_done = false;
                 if (!ok) {
                     timed_out = true;
                     break;
@@ -583,7 +591,19 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
                     if constexpr (MG) cyc_mark(msh.amg, team, kAmgMaxLevels - 3);
                     double v2[2] = {0.0, 0.0};
                     const R ra = static_cast<R>(alpha);
-                    for (int c = tid; c < nchunk; c += stride) {
+                    bool fused = false;
+                    if constexpr (MIXED && PC == 1) {
+                        if (fuse) {
+                            float* rn = rbuf[rsel ^ 1];
+                            cyc0_update_presmooth_v(level_view(w.mg, 0, rn, zc), r, rn, q, pnew, d, ra, P.mg_omega,
+                                                    Range{tid, stride}, &v2[0]);
+                            rsel ^= 1;
+                            r = rn;
+                            r0 = rn;
+                            fused = true;
+                        }
+                    }
+                    for (int c = fused ? nchunk : tid; c < nchunk; c += stride) {
                         const int k = c * W;
                         R pk[W], qk[W], rk[W], xk[W];
                         ldv<R, W>(pnew + k, pk);
@@ -624,6 +644,7 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
                             use_p = true;
                         }
                         rr = rr_new;
+                        pre0_done = fused;
                         continue;
                     }
                 }
