@@ -1117,8 +1117,8 @@ __device__ void amg_coarse(const AV& L, const float* inv, bool dense, float om, 
 // z = B r0 on the team; rz, rzo receive this thread's partial sums of r0.z and r0.z_old.
 // Returns false on a timed-out wait.
 __device__ bool amg_vcycle(const AMGData& A, AMGShared& as, const float* r0, float* z, const float* zold,
-                           const float* cW0, const float* cS0, int nx0, float om, int block_cells, Team team, int tid,
-                           int stride,
+                           const float* cW0, const float* cS0, int nx0, float om, int block_cells, bool pre0_done,
+                           Team team, int tid, int stride,
                            unsigned* bar, long long spin, int* abort_flag, double* rz, double* rzo) {
     const int nl = as.nlev;
     const int Lc = nl - 1;
@@ -1137,9 +1137,13 @@ __device__ bool amg_vcycle(const AMGData& A, AMGShared& as, const float* r0, flo
     for (int l = 0; l < lg; l++) {
         const AV F = view(l), C = view(l + 1);
         cyc_mark(as, team, l);
-        if (l == 0 && v0) amg0_v<0>(F, F.b, F.x, om, tr, nullptr, nullptr, nullptr);
-        else amg_pre<true, true>(F, om, tr);
-        if (!sync()) return false;
+        // level 0's pre-smoothing may already be done by the fused Krylov update (whose
+        // reduction was the barrier)
+        if (!(l == 0 && v0 && pre0_done)) {
+            if (l == 0 && v0) amg0_v<0>(F, F.b, F.x, om, tr, nullptr, nullptr, nullptr);
+            else amg_pre<true, true>(F, om, tr);
+            if (!sync()) return false;
+        }
         if (l == 0 && v0) amg0_v<1>(F, F.x, F.t, om, tr, nullptr, nullptr, nullptr);
         else amg_resid<true, true>(F, tr);
         if (!sync()) return false;

@@ -238,7 +238,8 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
     // between two buffers
     float* rbuf[2] = {w.r32, w.r32b};
     int rsel = 0;
-    const bool fuse = MIXED && PC == 1 && W == 4 && w.mg.nlev > 1 && w.mg.L[0].N > P.block_cells;
+    const bool fuse = MIXED && PC != 0 && W == 4 &&
+                      (PC == 1 ? (w.mg.nlev > 1 && w.mg.L[0].N > P.block_cells) : N > P.block_cells);
     bool pre0_done = false;
     float* zc = w.mg.z;
     float* zo = w.mg.zold;
@@ -441,8 +442,9 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
                 double vz[2] = {0.0, 0.0};
                 bool ok;
                 if constexpr (PC == 2)
-                    ok = amg_vcycle(w.amg, msh.amg, r0, zc, zo, w.cW32, w.cS32, nx, P.mg_omega, P.block_cells, team,
-                                    tid, stride, w.bar, P.spin_limit, abort_flag, &vz[0], &vz[1]);
+                    ok = amg_vcycle(w.amg, msh.amg, r0, zc, zo, w.cW32, w.cS32, nx, P.mg_omega, P.block_cells,
+                                    pre0_done && msh.amg.nlev > 1, team, tid, stride, w.bar, P.spin_limit, abort_flag,
+                                    &vz[0], &vz[1]);
                 else
                     ok = vcycle(w.mg, msh.amg, r0, zc, zo, P.mg_omega, P.mg_over, P.block_cells, pre0_done, team, tid,
                                 stride, w.bar, P.spin_limit, abort_flag, &vz[0], &vz[1]);
@@ -592,11 +594,15 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
                     double v2[2] = {0.0, 0.0};
                     const R ra = static_cast<R>(alpha);
                     bool fused = false;
-                    if constexpr (MIXED && PC == 1) {
-                        if (fuse) {
+                    if constexpr (MIXED && PC != 0) {
+                        if (fuse && (PC == 1 || msh.amg.nlev > 1)) {
                             float* rn = rbuf[rsel ^ 1];
-                            cyc0_update_presmooth_v(level_view(w.mg, 0, rn, zc), r, rn, q, pnew, d, ra, P.mg_omega,
-                                                    Range{tid, stride}, &v2[0]);
+                            // the aggregation cycle pre-smooths into its level-0 scratch, the
+                            // algebraic one into the cycle's output z
+                            Lv L0 = level_view(w.mg, 0, rn, zc);
+                            if constexpr (PC == 2) L0.xa = zc;
+                            cyc0_update_presmooth_v(L0, r, rn, q, pnew, d, ra, P.mg_omega, Range{tid, stride},
+                                                    &v2[0]);
                             rsel ^= 1;
                             r = rn;
                             r0 = rn;
