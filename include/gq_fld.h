@@ -73,9 +73,10 @@ typedef struct { double gamma, mu; } gq_eos;
 typedef struct { int side[4]; } gq_bc;
 
 /* Solver options.
- *   prec        GQ_PREC_FP64: FP64 Jacobi-PCG.  GQ_PREC_MIXED: FP32 Jacobi-PCG inside FP64
- *               iterative refinement (the FP64 residual b - A x is recomputed whenever the
- *               FP32 residual has fallen by inner_rtol, keeping the search direction).
+ *   prec        GQ_PREC_FP64: FP64 PCG.  GQ_PREC_MIXED: FP32 PCG inside FP64 iterative
+ *               refinement (the FP64 residual b - A x is recomputed whenever the FP32
+ *               residual has fallen by inner_rtol, keeping the search direction).  The
+ *               multigrid preconditioners run in FP32 for both.
  *   limiter     GQ_LIMITER_LP (Levermore-Pomraning rational form), _MINERBO (Eq. limiter),
  *               _NONE (lambda = 1/3).
  *   rtol        stop when max_k |b - A x|_k / (A_kk |x_k|) <= rtol (the cell-wise relative

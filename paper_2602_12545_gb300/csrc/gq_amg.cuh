@@ -19,7 +19,9 @@
 //              kAmgPmax largest kept and rescaled to the same row sum; C points inject
 //   A_{l+1}    P^T A_l P, one coarse row per thread: the fine rows that interpolate from
 //              coarse point c are c's own point and F neighbours of it, so the product
-//              is gathered without atomics (counted, scanned, then filled)
+//              is gathered without atomics; rows are computed once, staged at the pool
+//              tails and moved to the places a scan gives them (one warp per row when a
+//              row is too long for a thread's table)
 // Coarsening stops at <= kCoarseMax rows (dense inverse), when a level does not shrink,
 // or when a pool would overflow (the coarsest level is then smoothed instead).
 // The V-cycle works on the Jacobi-scaled levels A^_l = S_l A_l S_l (unit diagonal, FP32)

@@ -1,17 +1,22 @@
-// Persistent Jacobi-preconditioned conjugate-gradient solve of the reduced FLD system
-// (the Krylov step of Sec. 3.2.1, with a residual-based stop in the spirit of
+// Persistent preconditioned conjugate-gradient solve of the reduced FLD system (the
+// Krylov step of Sec. 3.2.1, with a residual-based stop in the spirit of
 // Eq. linearsystem).
 //
 // The system is solved in Jacobi-scaled form A^ y = b^ with A^ = S A S (unit diagonal,
-// off-diagonals -c_f = -w_f s_k s_m), so Jacobi-PCG on A is plain CG on A^ and the
-// matrix-free 5-point product reads two coefficient arrays per cell: c_W (face to the
-// west neighbour) and c_S (face to the south neighbour); the east and north
-// coefficients of cell k are c_W[k+1] and c_S[k+nx] (zero across the boundary).
+// off-diagonals -c_f = -w_f s_k s_m); the matrix-free 5-point product reads two
+// coefficient arrays per cell: c_W (face to the west neighbour) and c_S (face to the
+// south neighbour); the east and north coefficients of cell k are c_W[k+1] and
+// c_S[k+nx] (zero across the boundary).  The preconditioner is Jacobi (plain CG on A^),
+// one V-cycle of 2 x 2 aggregation multigrid (gq_mg.cuh) or one V-cycle of classical
+// algebraic multigrid built in the kernel's prologue (gq_amg.cuh); with multigrid the
+// directions use the Polak-Ribiere beta.
 //
-// One cooperative launch runs the whole solve.  Each iteration is two passes separated
-// by team-wide reductions:
-//   S: p = r + beta p_old (p double-buffered), q = A^ p, partial p.q
+// One cooperative launch runs the whole solve.  Each iteration is the preconditioner
+// and two passes separated by team-wide reductions:
+//   S: p = z + beta p_old (p double-buffered), q = A^ p, partial p.q
 //   U: x += alpha p, r -= alpha q, partial r.r (FP64 path: also max |r_k / y_k|)
+// In the mixed multigrid paths with a vectorised level 0, U is fused with the next
+// cycle's first level-0 sweep (the residual alternates between two buffers).
 // A thread handles W consecutive cells of one row with 16-byte loads (W = 4 in FP32,
 // 2 in FP64) when nx is a multiple of W, one cell otherwise.  All blocks reduce the
 // per-block partials in the same order, so every block takes bitwise-identical control
