@@ -189,10 +189,16 @@ def traffic_from_profile(kernel_tag, src_hash):
 
 
 def kernel_source_hash():
+    """Hash of the solver kernel's sources with comments and blank space removed, so that
+    a committed ncu figure stays attached to the code it was measured on."""
+    import re
     h = hashlib.sha256()
     for name in ("gq_pcg.cu", "gq_mg.cuh", "gq_amg.cuh", "gq_device.cuh", "gq_internal.h"):
-        with open(os.path.join(ROOT, "paper_2602_12545_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_2602_12545_gb300", "csrc", name)) as f:
+            src = f.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update("".join(src.split()).encode())
     return h.hexdigest()
 
 
