@@ -179,6 +179,21 @@ gq_status gq_fld_step(gq_fld_plan *plan, const double *rho, double *e_g, double 
                       const gq_opacity_law *opacity, const gq_eos *eos, double dt, const gq_bc *bc,
                       const gq_solver_opts *opts, void *stream, gq_step_info *info);
 
+/* The hydro step dt_total split into n_sub implicit FLD steps of geometrically growing
+ * length (Sec. 3.2, Eq. subtimesteps): dt_i = dt_0 q_t^(i-1), i = 1..n_sub, with
+ * dt_0 = dt_total (1 - q_t) / (1 - q_t^n_sub), so that they add up to dt_total (q_t = 1:
+ * equal sub-steps).  Each sub-step is gq_fld_step from the state the previous one left,
+ * so opacities, limiter and coefficients are re-evaluated.  Arguments as gq_fld_step;
+ * n_sub >= 1, q_t > 0 (the paper uses 1 < q_t < 2), dt_total > 0.  info: iterations and
+ * refinements summed, residuals the largest of the sub-steps, energy_before of the first
+ * and energy_after of the last sub-step, timings summed.  A sub-step that ends with
+ * GQ_ERR_NOT_CONVERGED does not stop the series (the call then returns that status);
+ * any other error stops it and is returned. */
+gq_status gq_fld_step_subcycled(gq_fld_plan *plan, const double *rho, double *e_g, double *E_r,
+                                double *T_g_out, const gq_opacity_law *opacity, const gq_eos *eos,
+                                double dt_total, int n_sub, double q_t, const gq_bc *bc,
+                                const gq_solver_opts *opts, void *stream, gq_step_info *info);
+
 /* Release a plan and its device memory (NULL is ignored). */
 void gq_fld_destroy(gq_fld_plan *plan);
 

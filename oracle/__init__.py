@@ -201,3 +201,33 @@ def step(prob, method: str = "lu", tol: float = 1e-15, V=None, Ax=None, Ay=None)
     return {"E_r": E, "T_g": T, "e_g": eg, "iterations": int(info[0]), "cell_residual": info[1],
             "l2_residual": info[2], "energy_before": info[3], "energy_after": info[4],
             "Fx": Fx, "Fy": Fy, "status": rc}
+
+
+def subcycle_dts(dt_total: float, n_sub: int, q_t: float) -> list:
+    """Sub-step lengths of Eq. subtimesteps (Sec. 3.2): dt_i = dt_0 q^(i-1), i = 1..n_sub,
+    dt_0 = dt_total (1 - q) / (1 - q^n_sub), so that they add up to the hydro step;
+    q = 1, the limit of the formula, gives equal sub-steps."""
+    if q_t == 1.0:
+        return [dt_total / n_sub] * n_sub
+    dt0 = dt_total * (1.0 - q_t) / (1.0 - q_t ** n_sub)
+    return [dt0 * q_t ** (i - 1) for i in range(1, n_sub + 1)]
+
+
+def step_subcycled(prob, n_sub: int, q_t: float, method: str = "lu", tol: float = 1e-15) -> dict:
+    """prob.dt split into n_sub implicit steps (Eq. subtimesteps), each taken from the state
+    the previous one left, so opacities, limiter and coefficients are re-evaluated."""
+    import copy
+    P = copy.copy(prob)
+    P.E_r = np.array(prob.E_r, dtype=np.float64, copy=True)
+    P.e_g = np.array(prob.e_g, dtype=np.float64, copy=True)
+    first, out, its = None, None, 0
+    for dt in subcycle_dts(prob.dt, n_sub, q_t):
+        P.dt = dt
+        out = step(P, method, tol)
+        if first is None:
+            first = out
+        P.E_r = out["E_r"].copy()
+        P.e_g = out["e_g"].copy()
+        its += out["iterations"]
+    return {"E_r": out["E_r"], "T_g": out["T_g"], "e_g": out["e_g"], "iterations": its,
+            "energy_before": first["energy_before"], "energy_after": out["energy_after"]}

@@ -600,4 +600,47 @@ gq_status gq_fld_step(gq_fld_plan* P, const double* rho, double* e_g, double* E_
     return status;
 }
 
+gq_status gq_fld_step_subcycled(gq_fld_plan* P, const double* rho, double* e_g, double* E_r, double* T_g_out,
+                                const gq_opacity_law* op, const gq_eos* eos, double dt_total, int n_sub, double q_t,
+                                const gq_bc* bc, const gq_solver_opts* opts, void* stream, gq_step_info* info) {
+    if (info) {
+        std::memset(info, 0, sizeof(*info));
+        info->status = GQ_ERR_INVALID_ARG;
+    }
+    if (!P || n_sub < 1 || !(q_t > 0.0) || !std::isfinite(q_t) || !(dt_total > 0.0) || !std::isfinite(dt_total))
+        return GQ_ERR_INVALID_ARG;
+    // Eq. subtimesteps; q_t = 1 is the limit of the formula (equal sub-steps)
+    const double dt0 = q_t == 1.0 ? dt_total / n_sub : dt_total * (1.0 - q_t) / (1.0 - std::pow(q_t, n_sub));
+    if (!(dt0 > 0.0) || !std::isfinite(dt0)) return GQ_ERR_INVALID_ARG;
+    gq_step_info acc{};
+    gq_status result = GQ_OK;
+    for (int i = 0; i < n_sub; i++) {
+        const double dt = q_t == 1.0 ? dt0 : dt0 * std::pow(q_t, i);
+        gq_step_info si{};
+        const gq_status s = gq_fld_step(P, rho, e_g, E_r, T_g_out, op, eos, dt, bc, opts, stream, &si);
+        if (i == 0) acc.energy_before = si.energy_before;
+        acc.iterations += si.iterations;
+        acc.refinements += si.refinements;
+        acc.rel_residual = std::max(acc.rel_residual, si.rel_residual);
+        acc.rel_residual_l2 = std::max(acc.rel_residual_l2, si.rel_residual_l2);
+        acc.energy_after = si.energy_after;
+        acc.solve_blocks = si.solve_blocks;
+        acc.t_setup_ms += si.t_setup_ms;
+        acc.t_solve_ms += si.t_solve_ms;
+        acc.t_finish_ms += si.t_finish_ms;
+        acc.t_precond_ms += si.t_precond_ms;
+        acc.precond_levels = si.precond_levels;
+        if (s == GQ_ERR_NOT_CONVERGED) {
+            result = s;
+        } else if (s != GQ_OK) {
+            result = s;
+            break;
+        }
+    }
+    acc.t_iter_us = acc.iterations > 0 ? (float)(1e3 * (acc.t_solve_ms - acc.t_precond_ms) / acc.iterations) : 0.f;
+    acc.status = result;
+    if (info) *info = acc;
+    return result;
+}
+
 }  // extern "C"

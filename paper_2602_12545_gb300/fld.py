@@ -114,8 +114,10 @@ class FLDPlan:
     def step(self, rho: torch.Tensor, e_g: torch.Tensor, E_r: torch.Tensor, T_out: Optional[torch.Tensor] = None,
              *, opacity_R: Sequence[float], opacity_P: Sequence[float], gamma: float, mu: float, dt: float,
              bc: Sequence[int], opts: SolverOptions, stream: Optional[torch.cuda.Stream] = None,
-             check: bool = True) -> dict:
-        """One implicit step; e_g and E_r are updated in place, T_out receives T_g^{n+1}."""
+             check: bool = True, n_sub: int = 0, q_t: float = 1.0) -> dict:
+        """One implicit step; e_g and E_r are updated in place, T_out receives T_g^{n+1}.
+        With n_sub >= 1, dt is split into n_sub geometric sub-steps of ratio q_t
+        (gq_fld_step_subcycled)."""
         for t, n in ((rho, "rho"), (e_g, "e_g"), (E_r, "E_r")):
             self._check(t, n)
         if T_out is not None:
@@ -128,14 +130,20 @@ class FLDPlan:
         o = opts.to_c()
         info = N.StepInfo()
         st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
-        rc = N.load().gq_fld_step(self._h, rho.data_ptr(), e_g.data_ptr(), E_r.data_ptr(),
-                                  T_out.data_ptr() if T_out is not None else None,
-                                  ctypes.byref(op), ctypes.byref(eos), float(dt), ctypes.byref(b),
-                                  ctypes.byref(o), ctypes.c_void_p(st), ctypes.byref(info))
+        T_ptr = T_out.data_ptr() if T_out is not None else None
+        if n_sub >= 1:
+            rc = N.load().gq_fld_step_subcycled(self._h, rho.data_ptr(), e_g.data_ptr(), E_r.data_ptr(), T_ptr,
+                                                ctypes.byref(op), ctypes.byref(eos), float(dt), int(n_sub),
+                                                float(q_t), ctypes.byref(b), ctypes.byref(o), ctypes.c_void_p(st),
+                                                ctypes.byref(info))
+        else:
+            rc = N.load().gq_fld_step(self._h, rho.data_ptr(), e_g.data_ptr(), E_r.data_ptr(), T_ptr,
+                                      ctypes.byref(op), ctypes.byref(eos), float(dt), ctypes.byref(b),
+                                      ctypes.byref(o), ctypes.c_void_p(st), ctypes.byref(info))
         out = info.as_dict()
         out["status"] = rc
         if check and rc not in (N.GQ_OK,):
-            raise N.GQError(rc, "gq_fld_step")
+            raise N.GQError(rc, "gq_fld_step_subcycled" if n_sub >= 1 else "gq_fld_step")
         return out
 
 
@@ -149,12 +157,13 @@ def device_fields(p: FLDProblem, device="cuda"):
 
 
 def step_problem(plan: FLDPlan, p: FLDProblem, rho, e_g, E_r, T_out=None, *, prec=None, rtol=None,
-                 check=True, **kw) -> dict:
-    """One step of problem p with its own settings (limiter, bc, dt, precision, rtol)."""
+                 check=True, n_sub=0, q_t=1.0, **kw) -> dict:
+    """One step of problem p with its own settings (limiter, bc, dt, precision, rtol);
+    n_sub >= 1 sub-cycles it (Eq. subtimesteps)."""
     opts = SolverOptions(prec=p.precision if prec is None else prec, limiter=p.limiter,
                          rtol=p.rtol if rtol is None else rtol, **kw)
     return plan.step(rho, e_g, E_r, T_out, opacity_R=p.opacity_R, opacity_P=p.opacity_P, gamma=p.gamma,
-                     mu=p.mu, dt=p.dt, bc=p.bc, opts=opts, check=check)
+                     mu=p.mu, dt=p.dt, bc=p.bc, opts=opts, check=check, n_sub=n_sub, q_t=q_t)
 
 
 class FLDBatch:

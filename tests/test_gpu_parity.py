@@ -242,3 +242,50 @@ def test_loose_refinement_trigger_still_converges(fld, orc):
     out = run_gpu(fld, P, W.PREC_MIXED, 1e-11, precond=1, inner_rtol=0.3)
     assert out["info"]["status"] == 0, out["info"]
     check_parity(out, ref, MIXED_GATE)
+
+
+# ----------------------------------------------------------------------------
+# sub-cycling (Eq. subtimesteps): n_sub geometric sub-steps against the oracle's
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case,prec,n_sub,q_t", [
+    ("c0", W.PREC_FP64, 5, 1.4),
+    ("c0", W.PREC_MIXED, 5, 1.4),
+    ("sph", W.PREC_FP64, 3, 1.2),
+    ("sph", W.PREC_MIXED, 6, 1.0),
+])
+def test_subcycled_step(fld, orc, case, prec, n_sub, q_t):
+    P = W.config0() if case == "c0" else W.random_small(40, 24, W.SPHERICAL, (0, 1, 0, 0), 41, dt=3e4)
+    ref = orc.step_subcycled(P, n_sub, q_t)
+    cond = componentwise_condition(orc, P, ref["E_r"])
+    rtol = 1e-12 if prec == W.PREC_FP64 else 1e-10
+    out = run_gpu(fld, P, prec, rtol, n_sub=n_sub, q_t=q_t)
+    assert out["info"]["status"] == 0, out["info"]
+    check_parity_conditioned(out, ref, FP64_GATE if prec == W.PREC_FP64 else MIXED_GATE, cond)
+    assert out["info"]["energy_before"] == pytest.approx(ref["energy_before"], rel=1e-12)
+
+
+def test_subcycled_step_rejects_bad_series(fld):
+    """n_sub < 1, q_t <= 0 or not finite: GQ_ERR_INVALID_ARG before any work (fields kept)."""
+    import ctypes
+    import torch
+    from paper_2602_12545_gb300 import _native as N
+    P = W.config0()
+    plan = fld.FLDPlan.for_problem(P)
+    rho, e_g, E, T = fld.device_fields(P)
+    E0 = E.clone()
+    op = N.OpacityLaw(*[float(v) for v in tuple(P.opacity_R) + tuple(P.opacity_P)])
+    eos = N.Eos(float(P.gamma), float(P.mu))
+    bc = N.Bc()
+    o = fld.SolverOptions(prec=0, limiter=P.limiter, rtol=1e-10).to_c()
+    st = torch.cuda.current_stream().cuda_stream
+    for n_sub, q_t in ((0, 1.2), (-2, 1.2), (3, 0.0), (3, -1.0), (3, float("nan")), (3, float("inf"))):
+        info = N.StepInfo()
+        rc = N.load().gq_fld_step_subcycled(plan._h, rho.data_ptr(), e_g.data_ptr(), E.data_ptr(), T.data_ptr(),
+                                            ctypes.byref(op), ctypes.byref(eos), float(P.dt), n_sub, q_t,
+                                            ctypes.byref(bc), ctypes.byref(o), ctypes.c_void_p(st),
+                                            ctypes.byref(info))
+        assert rc == N.GQ_ERR_INVALID_ARG, (n_sub, q_t, rc)
+    torch.cuda.synchronize()
+    assert torch.equal(E, E0)
+    plan.close()

@@ -413,3 +413,49 @@ def test_free_streaming_bound(orc, kind):
     En = out["E_r"]
     Fn = np.abs(out["Fx"][:, 1:-1])
     assert np.all(Fn <= C_LIGHT * np.maximum(En[:, 1:], En[:, :-1]))
+
+
+# ---------------------------------------------------------------------------
+# sub-cycling (Eq. subtimesteps)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,q", [(1, 1.3), (5, 1.4), (50, 1.2), (6, 1.0)])
+def test_subcycle_series_fills_the_step(orc, n, q):
+    """The sub-steps are a geometric series with ratio q that adds up to the hydro step."""
+    dts = orc.subcycle_dts(3.7e4, n, q)
+    assert len(dts) == n and min(dts) > 0
+    assert math.fsum(dts) == pytest.approx(3.7e4, rel=1e-14)
+    for a, b in zip(dts, dts[1:]):
+        assert b / a == pytest.approx(q, rel=1e-13)
+
+
+def test_subcycle_single_substep_is_one_step(orc):
+    P = W.random_small(9, 7, W.CARTESIAN, (0, 1, 0, 0), 31)
+    a = orc.step(P, "lu")
+    b = orc.step_subcycled(P, 1, 1.3)
+    for f in ("E_r", "T_g", "e_g"):
+        assert np.array_equal(a[f], b[f])
+
+
+def test_subcycle_conserves_energy_with_reflecting_walls(orc):
+    P = W.random_small(12, 10, W.CARTESIAN, (0, 0, 0, 0), 32)
+    out = orc.step_subcycled(P, 6, 1.3)
+    assert abs(out["energy_after"] - out["energy_before"]) <= 1e-12 * out["energy_before"]
+
+
+def test_subcycle_follows_the_ode_closer_than_one_step(orc):
+    """Radiation-gas exchange in a uniform box (Sec. 5.1.1): one backward-Euler step of the
+    whole interval overshoots the stiff exchange; 50 geometric sub-steps with q = 1.2 (the
+    paper's choice for this test) stay close to the exact ODE."""
+    g = _golden("coupling_test.txt")
+    rho, kP, E0 = float(g["rho"][0]), float(g["kappa_P"][0]), float(g["E_r"][0])
+    e0 = 1e10
+    cv = rho * K_B / ((5.0 / 3.0 - 1.0) * float(g["mu"][0]) * M_H)
+    dt = 2e-7
+    P = _uniform_problem(2, 2, 1e10, rho, e0 / cv, E0, dt, kR=(kP, 0, 1, 0), kP=(kP, 0, 1, 0))
+    P.e_g[:] = e0
+    E_ode, e_ode = _ode(cv, rho * kP * C_LIGHT, e0, E0, np.array([0.0, dt]))
+    one = orc.step(P, "lu")["e_g"][0, 0]
+    sub = orc.step_subcycled(P, 50, 1.2)["e_g"][0, 0]
+    err_one, err_sub = abs(one - e_ode[-1]) / e_ode[-1], abs(sub - e_ode[-1]) / e_ode[-1]
+    assert err_sub < 0.2 * err_one, (err_one, err_sub)
