@@ -215,12 +215,16 @@ def subcycle_dts(dt_total: float, n_sub: int, q_t: float) -> list:
 
 def step_subcycled(prob, n_sub: int, q_t: float, method: str = "lu", tol: float = 1e-15) -> dict:
     """prob.dt split into n_sub implicit steps (Eq. subtimesteps), each taken from the state
-    the previous one left, so opacities, limiter and coefficients are re-evaluated."""
+    the previous one left, so opacities, limiter and coefficients are re-evaluated.  Fx, Fy:
+    the radiative face flux of the hydro step, the sub-steps' post-step fluxes weighted by
+    dt_i / dt (so that dt times it is the energy each face carried)."""
     import copy
     P = copy.copy(prob)
     P.E_r = np.array(prob.E_r, dtype=np.float64, copy=True)
     P.e_g = np.array(prob.e_g, dtype=np.float64, copy=True)
     first, out, its = None, None, 0
+    Fx = np.zeros((prob.ny, prob.nx + 1))
+    Fy = np.zeros((prob.ny + 1, prob.nx))
     for dt in subcycle_dts(prob.dt, n_sub, q_t):
         P.dt = dt
         out = step(P, method, tol)
@@ -229,5 +233,7 @@ def step_subcycled(prob, n_sub: int, q_t: float, method: str = "lu", tol: float 
         P.E_r = out["E_r"].copy()
         P.e_g = out["e_g"].copy()
         its += out["iterations"]
+        Fx += (dt / prob.dt) * out["Fx"]
+        Fy += (dt / prob.dt) * out["Fy"]
     return {"E_r": out["E_r"], "T_g": out["T_g"], "e_g": out["e_g"], "iterations": its,
-            "energy_before": first["energy_before"], "energy_after": out["energy_after"]}
+            "energy_before": first["energy_before"], "energy_after": out["energy_after"], "Fx": Fx, "Fy": Fy}

@@ -459,3 +459,22 @@ def test_subcycle_follows_the_ode_closer_than_one_step(orc):
     sub = orc.step_subcycled(P, 50, 1.2)["e_g"][0, 0]
     err_one, err_sub = abs(one - e_ode[-1]) / e_ode[-1], abs(sub - e_ode[-1]) / e_ode[-1]
     assert err_sub < 0.2 * err_one, (err_one, err_sub)
+
+
+def test_subcycled_flux_carries_the_lost_energy(orc):
+    """The hydro step's flux (sub-step fluxes weighted by dt_i / dt): dt times the
+    area-weighted flux through the Milne faces equals the energy the grid lost over all
+    sub-steps, and reflecting faces carry none."""
+    nx, ny, dx = 40, 3, 1e10
+    sigma = 1e-9
+    rng = np.random.default_rng(3)
+    E = 1e4 * (1 + 0.3 * rng.random((ny, nx)))
+    rho = 1e-10
+    P = _uniform_problem(nx, ny, dx, rho, 10.0, E, 3e3, kR=(sigma / rho, 0, 1, 0), kP=(0.0, 0, 1, 0),
+                         bc=(1, 1, 0, 0), limiter=W.LIMITER_NONE)
+    out = orc.step_subcycled(P, 6, 1.4)
+    lost = out["energy_before"] - out["energy_after"]
+    through = P.dt * dx * (out["Fx"][:, nx].sum() - out["Fx"][:, 0].sum())
+    assert lost > 0
+    assert lost == pytest.approx(through, rel=1e-10)
+    assert np.all(out["Fy"][0] == 0) and np.all(out["Fy"][-1] == 0)
