@@ -188,11 +188,18 @@ gq_status gq_fld_step(gq_fld_plan *plan, const double *rho, double *e_g, double 
  * refinements summed, residuals the largest of the sub-steps, energy_before of the first
  * and energy_after of the last sub-step, timings summed.  A sub-step that ends with
  * GQ_ERR_NOT_CONVERGED does not stop the series (the call then returns that status);
- * any other error stops it and is returned. */
+ * any other error stops it and is returned.
+ *   Fx, Fy   [ny][nx+1], [ny+1][nx] device (each may be NULL): the radiative flux of the
+ *            hydro step through every face, erg cm^-2 s^-1, positive along +x / +y: the
+ *            sub-steps' fluxes -D grad E (their own D, and E after the sub-step) weighted
+ *            by dt_i / dt_total, so that dt_total times it is the energy the face carried
+ *            (the accumulation of Sec. 3.2.1).  Reflecting faces carry 0; Milne faces
+ *            D_b E / (h (1 + k)) outward. */
 gq_status gq_fld_step_subcycled(gq_fld_plan *plan, const double *rho, double *e_g, double *E_r,
                                 double *T_g_out, const gq_opacity_law *opacity, const gq_eos *eos,
                                 double dt_total, int n_sub, double q_t, const gq_bc *bc,
-                                const gq_solver_opts *opts, void *stream, gq_step_info *info);
+                                const gq_solver_opts *opts, double *Fx, double *Fy, void *stream,
+                                gq_step_info *info);
 
 /* Release a plan and its device memory (NULL is ignored). */
 void gq_fld_destroy(gq_fld_plan *plan);

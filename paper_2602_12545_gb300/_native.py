@@ -136,7 +136,8 @@ SIGNATURES = {
     "gq_fld_step_subcycled": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.POINTER(OpacityLaw), ctypes.POINTER(Eos),
                                              ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.POINTER(Bc),
-                                             ctypes.POINTER(SolverOpts), ctypes.c_void_p, ctypes.POINTER(StepInfo)]),
+                                             ctypes.POINTER(SolverOpts), ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.POINTER(StepInfo)]),
     "gq_fld_precond_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(PrecondInfo)]),
     "gq_fld_step_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,

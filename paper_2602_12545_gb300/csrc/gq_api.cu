@@ -602,7 +602,8 @@ gq_status gq_fld_step(gq_fld_plan* P, const double* rho, double* e_g, double* E_
 
 gq_status gq_fld_step_subcycled(gq_fld_plan* P, const double* rho, double* e_g, double* E_r, double* T_g_out,
                                 const gq_opacity_law* op, const gq_eos* eos, double dt_total, int n_sub, double q_t,
-                                const gq_bc* bc, const gq_solver_opts* opts, void* stream, gq_step_info* info) {
+                                const gq_bc* bc, const gq_solver_opts* opts, double* Fx, double* Fy, void* stream,
+                                gq_step_info* info) {
     if (info) {
         std::memset(info, 0, sizeof(*info));
         info->status = GQ_ERR_INVALID_ARG;
@@ -618,6 +619,23 @@ gq_status gq_fld_step_subcycled(gq_fld_plan* P, const double* rho, double* e_g, 
         const double dt = q_t == 1.0 ? dt0 : dt0 * std::pow(q_t, i);
         gq_step_info si{};
         const gq_status s = gq_fld_step(P, rho, e_g, E_r, T_g_out, op, eos, dt, bc, opts, stream, &si);
+        if ((Fx || Fy) && (s == GQ_OK || s == GQ_ERR_NOT_CONVERGED)) {
+            // this sub-step's flux, weighted by its share of the hydro step (the workspace
+            // still holds its coefficients)
+            gq::StepParams sp{};
+            gq::SolveParams pp{};
+            gq_status vs = gq::make_step_params(P, rho, e_g, E_r, T_g_out, op, eos, dt, bc, opts, &sp, &pp, nullptr);
+            cudaError_t e = vs == GQ_OK ? cudaSuccess : cudaErrorInvalidValue;
+            if (e == cudaSuccess)
+                e = gq::launch_face_flux(sp, P->geo, P->ws, dt / dt_total, i > 0, Fx, Fy, P->setup_blocks,
+                                         static_cast<cudaStream_t>(stream));
+            if (e == cudaSuccess) e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                result = vs == GQ_OK ? GQ_ERR_CUDA : vs;
+                break;
+            }
+        }
         if (i == 0) acc.energy_before = si.energy_before;
         acc.iterations += si.iterations;
         acc.refinements += si.refinements;

@@ -223,6 +223,8 @@ cudaError_t launch_setup(const StepParams& sp, const DeviceGeometry& g, const Wo
 cudaError_t launch_solve(const SolveParams& p, const Workspace& w, int grid, cudaStream_t st);
 cudaError_t launch_backsub(const StepParams& sp, const DeviceGeometry& g, const Workspace& w,
                            int setup_blocks, cudaStream_t st);
+cudaError_t launch_face_flux(const StepParams& sp, const DeviceGeometry& g, const Workspace& w, double weight,
+                             bool accumulate, double* Fx, double* Fy, int nblk, cudaStream_t st);
 int solve_max_blocks_per_sm();
 int batch_solve_max_blocks_per_sm();
 cudaError_t launch_batch_setup(const BatchArgs& a, int total_setup_blocks, cudaStream_t st);

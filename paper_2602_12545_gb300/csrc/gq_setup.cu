@@ -357,6 +357,58 @@ cudaError_t launch_batch_finish(const BatchArgs& a, int total, cudaStream_t st) 
     return cudaGetLastError();
 }
 
+// Radiative face flux of a finished step (F = -D grad E with the step's D and E^{n+1},
+// positive along +x / +y), times weight, written (accumulate = 0) or added to Fx
+// [ny][nx+1] and Fy [ny+1][nx].  Interior faces: D / d from the face weight w = dt A D / d
+// (recovered as c / (s_k s_m) from the scaled coupling); Milne faces: D_b E / (h (1 + k)),
+// outward; reflecting faces: 0.
+__global__ void k_face_flux(StepParams sp, DeviceGeometry g, Workspace w, double weight, int accumulate, double* Fx,
+                            double* Fy) {
+    const int nx = sp.nx, ny = sp.ny;
+    const long long nfx = (long long)ny * (nx + 1), nfy = (long long)(ny + 1) * nx;
+    const double* E = sp.E;
+    const double* s = w.dloc;
+    auto milne = [&](double sig, double h, double Ek) {
+        const double kk = 2.0 / (3.0 * sig * h);
+        return kC * limiter(sp.limiter, 1.5) / sig * Ek / (h * (1.0 + kk));
+    };
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nfx + nfy;
+         t += (long long)gridDim.x * blockDim.x) {
+        double F = 0.0;
+        if (t < nfx) {
+            const int j = (int)(t / (nx + 1)), i = (int)(t - (long long)j * (nx + 1));
+            if (i > 0 && i < nx) {
+                const int k = j * nx + i;
+                const double gA = g.gx[t];
+                if (gA > 0.0) F = w.wW[k] / (s[k] * s[k - 1]) / (sp.dt * gA) * (E[k - 1] - E[k]) / g.dxf[i];
+            } else if (sp.bc[i == 0 ? 0 : 1] == GQ_BC_OUTFLOW_MILNE) {
+                const int k = j * nx + (i == 0 ? 0 : nx - 1);
+                F = (i == 0 ? -1.0 : 1.0) * milne(w.sig[k], g.dxf[i], E[k]);
+            }
+            if (Fx) Fx[t] = (accumulate ? Fx[t] : 0.0) + weight * F;
+        } else {
+            const long long f = t - nfx;
+            const int j = (int)(f / nx), i = (int)(f - (long long)j * nx);
+            if (j > 0 && j < ny) {
+                const int k = j * nx + i;
+                const double gA = g.gy[f];
+                if (gA > 0.0)
+                    F = w.wS[k] / (s[k] * s[k - nx]) / (sp.dt * gA) * (E[k - nx] - E[k]) / (g.ymet[i] * g.dyf[j]);
+            } else if (sp.bc[j == 0 ? 2 : 3] == GQ_BC_OUTFLOW_MILNE) {
+                const int k = j == 0 ? i : (ny - 1) * nx + i;
+                F = (j == 0 ? -1.0 : 1.0) * milne(w.sig[k], g.ymet[i] * g.dyf[j], E[k]);
+            }
+            if (Fy) Fy[f] = (accumulate ? Fy[f] : 0.0) + weight * F;
+        }
+    }
+}
+
+cudaError_t launch_face_flux(const StepParams& sp, const DeviceGeometry& g, const Workspace& w, double weight,
+                             bool accumulate, double* Fx, double* Fy, int nblk, cudaStream_t st) {
+    k_face_flux<<<nblk, kSetupThreads, 0, st>>>(sp, g, w, weight, accumulate ? 1 : 0, Fx, Fy);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_backsub(const StepParams& sp, const DeviceGeometry& g, const Workspace& w, int nblk,
                            cudaStream_t st) {
     k_backsub<<<nblk, kSetupThreads, 0, st>>>(sp, g, w);

@@ -114,10 +114,12 @@ class FLDPlan:
     def step(self, rho: torch.Tensor, e_g: torch.Tensor, E_r: torch.Tensor, T_out: Optional[torch.Tensor] = None,
              *, opacity_R: Sequence[float], opacity_P: Sequence[float], gamma: float, mu: float, dt: float,
              bc: Sequence[int], opts: SolverOptions, stream: Optional[torch.cuda.Stream] = None,
-             check: bool = True, n_sub: int = 0, q_t: float = 1.0) -> dict:
+             check: bool = True, n_sub: int = 0, q_t: float = 1.0, Fx: Optional[torch.Tensor] = None,
+             Fy: Optional[torch.Tensor] = None) -> dict:
         """One implicit step; e_g and E_r are updated in place, T_out receives T_g^{n+1}.
         With n_sub >= 1, dt is split into n_sub geometric sub-steps of ratio q_t
-        (gq_fld_step_subcycled)."""
+        (gq_fld_step_subcycled); Fx [ny][nx+1] and Fy [ny+1][nx] (float64 CUDA tensors) then
+        receive the hydro step's face flux."""
         for t, n in ((rho, "rho"), (e_g, "e_g"), (E_r, "E_r")):
             self._check(t, n)
         if T_out is not None:
@@ -132,9 +134,15 @@ class FLDPlan:
         st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
         T_ptr = T_out.data_ptr() if T_out is not None else None
         if n_sub >= 1:
+            for t, shape, name in ((Fx, (self.ny, self.nx + 1), "Fx"), (Fy, (self.ny + 1, self.nx), "Fy")):
+                if t is not None and (t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous()
+                                      or t.numel() != shape[0] * shape[1]):
+                    raise ValueError(f"{name} must be a contiguous float64 CUDA tensor of {shape[0]} x {shape[1]}")
             rc = N.load().gq_fld_step_subcycled(self._h, rho.data_ptr(), e_g.data_ptr(), E_r.data_ptr(), T_ptr,
                                                 ctypes.byref(op), ctypes.byref(eos), float(dt), int(n_sub),
-                                                float(q_t), ctypes.byref(b), ctypes.byref(o), ctypes.c_void_p(st),
+                                                float(q_t), ctypes.byref(b), ctypes.byref(o),
+                                                Fx.data_ptr() if Fx is not None else None,
+                                                Fy.data_ptr() if Fy is not None else None, ctypes.c_void_p(st),
                                                 ctypes.byref(info))
         else:
             rc = N.load().gq_fld_step(self._h, rho.data_ptr(), e_g.data_ptr(), E_r.data_ptr(), T_ptr,
@@ -157,13 +165,13 @@ def device_fields(p: FLDProblem, device="cuda"):
 
 
 def step_problem(plan: FLDPlan, p: FLDProblem, rho, e_g, E_r, T_out=None, *, prec=None, rtol=None,
-                 check=True, n_sub=0, q_t=1.0, **kw) -> dict:
+                 check=True, n_sub=0, q_t=1.0, Fx=None, Fy=None, **kw) -> dict:
     """One step of problem p with its own settings (limiter, bc, dt, precision, rtol);
     n_sub >= 1 sub-cycles it (Eq. subtimesteps)."""
     opts = SolverOptions(prec=p.precision if prec is None else prec, limiter=p.limiter,
                          rtol=p.rtol if rtol is None else rtol, **kw)
     return plan.step(rho, e_g, E_r, T_out, opacity_R=p.opacity_R, opacity_P=p.opacity_P, gamma=p.gamma,
-                     mu=p.mu, dt=p.dt, bc=p.bc, opts=opts, check=check, n_sub=n_sub, q_t=q_t)
+                     mu=p.mu, dt=p.dt, bc=p.bc, opts=opts, check=check, n_sub=n_sub, q_t=q_t, Fx=Fx, Fy=Fy)
 
 
 class FLDBatch:

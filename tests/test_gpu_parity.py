@@ -259,10 +259,28 @@ def test_subcycled_step(fld, orc, case, prec, n_sub, q_t):
     ref = orc.step_subcycled(P, n_sub, q_t)
     cond = componentwise_condition(orc, P, ref["E_r"])
     rtol = 1e-12 if prec == W.PREC_FP64 else 1e-10
-    out = run_gpu(fld, P, prec, rtol, n_sub=n_sub, q_t=q_t)
+    import torch
+    Fx = torch.full((P.ny, P.nx + 1), float("nan"), dtype=torch.float64, device="cuda")
+    Fy = torch.full((P.ny + 1, P.nx), float("nan"), dtype=torch.float64, device="cuda")
+    out = run_gpu(fld, P, prec, rtol, n_sub=n_sub, q_t=q_t, Fx=Fx, Fy=Fy)
     assert out["info"]["status"] == 0, out["info"]
-    check_parity_conditioned(out, ref, FP64_GATE if prec == W.PREC_FP64 else MIXED_GATE, cond)
+    gate = FP64_GATE if prec == W.PREC_FP64 else MIXED_GATE
+    check_parity_conditioned(out, ref, gate, cond)
     assert out["info"]["energy_before"] == pytest.approx(ref["energy_before"], rel=1e-12)
+    # accumulated face flux: a difference of neighbouring E values, so where the gradient
+    # is small its relative error is E / dE times that of E; gated norm-wise against the
+    # largest flux of the step, at 1000 times the field gate
+    fx, fy = Fx.cpu().numpy(), Fy.cpu().numpy()
+    scale = max(np.abs(ref["Fx"]).max(), np.abs(ref["Fy"]).max())
+    assert scale > 0
+    for got, want in ((fx, ref["Fx"]), (fy, ref["Fy"])):
+        assert np.isfinite(got).all()
+        err = np.abs(got - want).max() / scale
+        assert err <= 1e3 * gate, f"flux err {err:.3e}"
+    # reflecting sides carry nothing, exactly
+    for side, f in zip(P.bc, (fx[:, 0], fx[:, -1], fy[0, :], fy[-1, :])):
+        if side == 0:
+            assert (f == 0.0).all()
 
 
 def test_subcycled_step_rejects_bad_series(fld):
@@ -283,7 +301,7 @@ def test_subcycled_step_rejects_bad_series(fld):
         info = N.StepInfo()
         rc = N.load().gq_fld_step_subcycled(plan._h, rho.data_ptr(), e_g.data_ptr(), E.data_ptr(), T.data_ptr(),
                                             ctypes.byref(op), ctypes.byref(eos), float(P.dt), n_sub, q_t,
-                                            ctypes.byref(bc), ctypes.byref(o), ctypes.c_void_p(st),
+                                            ctypes.byref(bc), ctypes.byref(o), None, None, ctypes.c_void_p(st),
                                             ctypes.byref(info))
         assert rc == N.GQ_ERR_INVALID_ARG, (n_sub, q_t, rc)
     torch.cuda.synchronize()
