@@ -29,7 +29,7 @@ class _Problem(ctypes.Structure):
         ("rho", _dp), ("eg", _dp), ("E", _dp),
         ("kR", ctypes.c_double * 4), ("kP", ctypes.c_double * 4),
         ("gamma", ctypes.c_double), ("mu", ctypes.c_double), ("dt", ctypes.c_double),
-        ("bc", ctypes.c_int * 4), ("limiter", ctypes.c_int),
+        ("bc", ctypes.c_int * 4), ("limiter", ctypes.c_int), ("S_adv", _dp),
     ]
 
 
@@ -53,6 +53,7 @@ def lib():
             L.orc_pcg.argtypes = [ctypes.c_int, _ip, _ip, _dp, _dp, _dp, ctypes.c_double, ctypes.c_int,
                                   _ip, _dp]
             L.orc_step.argtypes = [P, ctypes.c_int, ctypes.c_double, _dp, _dp, _dp, _dp, _dp, _dp]
+            L.orc_adv_source.argtypes = [P, _dp, _dp, _dp]
             _lib = L
     return _lib
 
@@ -81,7 +82,9 @@ class _Bound:
                      np.ascontiguousarray(prob.rho, dtype=np.float64),
                      np.ascontiguousarray(prob.e_g, dtype=np.float64),
                      np.ascontiguousarray(prob.E_r, dtype=np.float64)]
-        xf, yf, V_, Ax_, Ay_, rho, eg, E = self.arrs
+        S_adv = getattr(prob, "S_adv", None)
+        self.arrs.append(None if S_adv is None else np.ascontiguousarray(S_adv, dtype=np.float64).ravel())
+        xf, yf, V_, Ax_, Ay_, rho, eg, E, S = self.arrs
         s = _Problem()
         s.nx, s.ny, s.coord = prob.nx, prob.ny, int(prob.coord)
         s.xf, s.yf, s.V_in, s.Ax_in, s.Ay_in = _d(xf), _d(yf), _d(V_), _d(Ax_), _d(Ay_)
@@ -92,6 +95,7 @@ class _Bound:
             s.bc[t] = int(prob.bc[t])
         s.gamma, s.mu, s.dt = float(prob.gamma), float(prob.mu), float(prob.dt)
         s.limiter = int(prob.limiter)
+        s.S_adv = _d(S)
         self.s = s
 
     def ref(self):
@@ -130,6 +134,21 @@ def faces(prob, V=None, Ax=None, Ay=None) -> dict:
     if rc:
         raise RuntimeError(f"orc_faces failed ({rc})")
     return out
+
+
+def adv_source(prob, fx, fy) -> np.ndarray:
+    """Eq. adv: the explicit advection source S_adv [ny][nx] (erg cm^-3 s^-1) from face mass
+    fluxes fx [ny][nx+1], fy [ny+1][nx] (g cm^-2 s^-1, positive along +x / +y) and the
+    upwind e_r = E / rho of prob's fields."""
+    nx, ny = prob.nx, prob.ny
+    fx = np.ascontiguousarray(fx, dtype=np.float64).reshape(ny, nx + 1)
+    fy = np.ascontiguousarray(fy, dtype=np.float64).reshape(ny + 1, nx)
+    S = np.zeros((ny, nx))
+    b = _Bound(prob)
+    rc = lib().orc_adv_source(b.ref(), _d(fx), _d(fy), _d(S))
+    if rc:
+        raise RuntimeError(f"orc_adv_source failed ({rc})")
+    return S
 
 
 def _csr(n, rp, cl, vl, nnz):

@@ -22,6 +22,8 @@
  *     loses all accuracy once beta_P >> 1 (phi_5 = 1 + ... + beta_P), so it is only
  *     compared where the coupling is moderate;
  *   - T^{n+1} back-substituted from the psi row, e_g^{n+1} = e_g^n + C_V (T^{n+1} - T^n).
+ *   - the explicit advection source S_adv of Eq. adv (face mass flux times the upwind
+ *     e_r = E / rho, times g = dS / dV), which enters phi_11 as S_adv dt; S_g = 0.
  *
  * Readings where the paper is silent or inconsistent (each one is a named choice):
  *   - D > 0 (Eq. diffcoeff prints a minus sign; only D > 0 makes phi_5 diagonally
@@ -39,6 +41,8 @@
  *     lambda_b = lambda(3/2) and D_b = c lambda_b / sigma_k; the face flux
  *     D_b (E_k - E_b)/h acts like a face to a zero-energy ghost at distance h (1+k).
  *   - Reflecting boundary: no flux through the face.
+ *   - Eq. adv at a boundary face: the upwind e_r is that of the face's one cell (a
+ *     zero-gradient ghost), whichever way the given mass flux points.
  *   - Spherical-polar (r, theta), axisymmetric, the common factor 2 pi dropped:
  *     V = (r+^3 - r-^3)/3 (cos th- - cos th+), A_r = r^2 (cos th- - cos th+),
  *     A_th = sin th (r+^2 - r-^2)/2; volume centres r_c = int r dV / int dV and
@@ -327,7 +331,7 @@ static orc_coef cell_coef(const orc_problem *P, const orc_work *W, int i, int j)
     double T = W->T[k], T3 = T * T * T, T4 = T3 * T;
     C.phi5 = 1.0 + sum + W->betaP[k];
     C.phi6 = -4.0 * W->betaE[k] * aR * T3;
-    C.phi11 = P->E[k] - 3.0 * W->betaE[k] * aR * T4;   /* + (S_adv + S_g) dt = 0 here */
+    C.phi11 = P->E[k] - 3.0 * W->betaE[k] * aR * T4 + (P->S_adv ? P->S_adv[k] : 0.0) * P->dt;   /* S_g = 0 */
     C.psi5 = -W->betaP[k];
     C.psi6 = W->CV[k] + 4.0 * W->betaE[k] * aR * T3;
     C.psi11 = W->CV[k] * T + 3.0 * W->betaE[k] * aR * T4;
@@ -410,12 +414,54 @@ int orc_assemble_reduced(const orc_problem *P, int *rowptr, int *col, double *va
                 int f = order[t];
                 if (nb[f] >= 0) { col[nnz] = nb[f]; val[nnz++] = -w[f]; }
             }
-            rhs[k] = Vk * (P->E[k] + W.betaE[k] * aT4 * W.CV[k] / C.psi6);
+            double Eadv = P->E[k] + (P->S_adv ? P->S_adv[k] : 0.0) * P->dt;
+            rhs[k] = Vk * (Eadv + W.betaE[k] * aT4 * W.CV[k] / C.psi6);
             rowptr[k + 1] = nnz;
         }
     }
     work_free(&W);
     return nnz;
+}
+
+/* ------------------------------------------------------------------------- */
+/* explicit advection source (Eq. adv)                                         */
+/* ------------------------------------------------------------------------- */
+int orc_adv_source(const orc_problem *P, const double *fx, const double *fy, double *S)
+{
+    const int nx = P->nx, ny = P->ny, N = nx * ny;
+    double *V = malloc(sizeof(double) * N);
+    double *Ax = malloc(sizeof(double) * ny * (nx + 1));
+    double *Ay = malloc(sizeof(double) * (ny + 1) * nx);
+    double *xc = malloc(sizeof(double) * nx), *yc = malloc(sizeof(double) * ny);
+    int rc = (V && Ax && Ay && xc && yc) ? orc_geometry(P, V, Ax, Ay, xc, yc) : -2;
+    if (rc == 0) {
+        for (int j = 0; j < ny; j++) {
+            for (int i = 0; i < nx; i++) {
+                int k = j * nx + i;
+                /* the four faces of cell k: -x, +x, -y, +y; the neighbour across each
+                 * (-1 on a boundary) and the face's mass flux and area */
+                int nb[4] = {i > 0 ? k - 1 : -1, i < nx - 1 ? k + 1 : -1,
+                             j > 0 ? k - nx : -1, j < ny - 1 ? k + nx : -1};
+                double f[4] = {fx[j * (nx + 1) + i], fx[j * (nx + 1) + i + 1], fy[j * nx + i], fy[(j + 1) * nx + i]};
+                double A[4] = {Ax[j * (nx + 1) + i], Ax[j * (nx + 1) + i + 1], Ay[j * nx + i], Ay[(j + 1) * nx + i]};
+                double s = 0.0;
+                for (int t = 0; t < 4; t++) {
+                    /* the flow enters through a lower face when f > 0 and through an
+                     * upper face when f < 0; the upwind cell is then the neighbour */
+                    int lower = (t % 2) == 0;
+                    int in = lower ? f[t] > 0.0 : f[t] < 0.0;
+                    int up = (in && nb[t] >= 0) ? nb[t] : k;
+                    double er = P->E[up] / P->rho[up];
+                    double g = A[t] / V[k];
+                    /* lower faces add g f e_r, upper faces subtract it */
+                    s += (lower ? 1.0 : -1.0) * g * f[t] * er;
+                }
+                S[k] = s;
+            }
+        }
+    }
+    free(V); free(Ax); free(Ay); free(xc); free(yc);
+    return rc;
 }
 
 /* ------------------------------------------------------------------------- */

@@ -31,6 +31,8 @@ typedef struct {
     double dt;
     int bc[4];                /* 0 reflecting, 1 Milne outflow */
     int limiter;              /* 0 Levermore-Pomraning (rational), 1 Minerbo, 2 none (1/3) */
+    const double *S_adv;      /* optional explicit radiation source [ny][nx] (NULL: none),
+                                 erg cm^-3 s^-1: the S_adv of phi_11 (Eq. adv) */
 } orc_problem;
 
 /* physical constants (CGS) */
@@ -61,6 +63,11 @@ int orc_band_solve(int n, const int *rowptr, const int *col, const double *val, 
  * residual max_k |r_k| / (A_kk |x_k|) <= tol.  x holds the initial guess on entry. */
 int orc_pcg(int n, const int *rowptr, const int *col, const double *val, const double *rhs,
             double *x, double tol, int maxit, int *iters, double *crit);
+
+/* Eq. adv: S_adv per cell from the face mass fluxes fx [ny][nx+1], fy [ny+1][nx]
+ * (g cm^-2 s^-1, positive along +x / +y) and the upwind specific radiation energy
+ * e_r = E / rho, with g = dS / dV (Eq. fldg).  A boundary face takes e_r of its one cell. */
+int orc_adv_source(const orc_problem *P, const double *fx, const double *fy, double *S);
 
 /* One implicit step.  method 0: banded LU on the reduced system; 1: CG on the reduced
  * system to the cell-wise tol; 2: banded LU on the paper-literal coupled system.  Outputs E^{n+1}, T^{n+1}, e_g^{n+1}.  info (may be NULL) receives

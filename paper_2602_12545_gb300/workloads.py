@@ -69,6 +69,7 @@ class FLDProblem:
     limiter: int = LIMITER_LP
     precision: int = PREC_FP64
     rtol: float = 1e-10
+    S_adv: Optional[np.ndarray] = None   # [ny][nx] explicit radiation source, erg cm^-3 s^-1
 
     @property
     def nx(self) -> int:
@@ -246,6 +247,53 @@ def random_small(nx: int, ny: int, coord: int, bc, seed: int, limiter: int = LIM
         dt = 10.0 ** rng.uniform(3.0, 6.0)
     return _pack(f"small_{'cart' if coord == CARTESIAN else 'sph'}{nx}x{ny}_s{seed}", coord, xf, yf,
                  rho, T, Trad, dt, bc=tuple(bc), limiter=limiter)
+
+
+def advected_packet(nx: int = 1024, v: float = 1.8e5, sigma_R: float = 1e7, E0: float = 2e5, cfl: float = 1.0,
+                    limiter: int = LIMITER_LP):
+    """The dynamical-diffusion set-up (Sec. 5, radiation advected by a uniform flow and
+    diffusing, no coupling): x in [-2, 14] cm, one row of unit height, rho = 1,
+    rho kappa_R = sigma_R, kappa_P = 0, T_g = 0.1 K, E_r = 1 with E0 / (2 dx) in the two
+    cells whose centres lie within dx of x = 0; reflecting radiation boundaries and the
+    mass flux rho v on every x face (the fixed inflow state); dt = cfl dx / v.  Returns
+    (problem, fx [1][nx+1], fy [2][nx])."""
+    xf = np.linspace(-2.0, 14.0, nx + 1)
+    dx = xf[1] - xf[0]
+    xc = 0.5 * (xf[:-1] + xf[1:])
+    rho = np.ones((1, nx))
+    T = np.full((1, nx), 0.1)
+    E = np.ones((1, nx))
+    E[0, np.abs(xc) < dx] = E0 / (2.0 * dx)
+    P = FLDProblem(name=f"packet{nx}", coord=CARTESIAN, x_faces=xf, y_faces=np.array([0.0, 1.0]), rho=rho,
+                   e_g=rho * T * EG_PER_RHO_T, E_r=E, dt=float(cfl * dx / v), bc=(BC_REFLECT,) * 4,
+                   opacity_R=(float(sigma_R), 0.0, 0.0, 0.0), opacity_P=(0.0, 0.0, 0.0, 0.0), limiter=limiter)
+    return P, np.full((1, nx + 1), v * 1.0), np.zeros((2, nx))
+
+
+def mass_fluxes(P: FLDProblem, seed: int, cfl: float = 0.05):
+    """Random face mass fluxes rho v (g cm^-2 s^-1) for problem P: v = cfl N(0,1) (clipped
+    to +-1) times the smaller width of the face's cells over dt, rho that of the cell the
+    flow comes from (a boundary face: its one cell).  Returns (fx [ny][nx+1], fy [ny+1][nx])."""
+    rng = np.random.default_rng(seed)
+    nx, ny = P.nx, P.ny
+    xf, yf = P.x_faces, P.y_faces
+    wx = np.broadcast_to(np.diff(xf)[None, :], (ny, nx))
+    if P.coord == CARTESIAN:
+        wy = np.broadcast_to(np.diff(yf)[:, None], (ny, nx))
+    else:
+        wy = np.diff(yf)[:, None] * (0.5 * (xf[:-1] + xf[1:]))[None, :]
+
+    def faces(w, rho, n_f, axis):
+        # pad with the edge cell on both sides so that face f sits between cells f-1 and f
+        wp = np.concatenate([np.take(w, [0], axis), w, np.take(w, [-1], axis)], axis)
+        rp = np.concatenate([np.take(rho, [0], axis), rho, np.take(rho, [-1], axis)], axis)
+        lo = [slice(None)] * 2; hi = [slice(None)] * 2
+        lo[axis] = slice(0, n_f); hi[axis] = slice(1, n_f + 1)
+        dmin = np.minimum(wp[tuple(lo)], wp[tuple(hi)])
+        v = cfl * np.clip(rng.standard_normal(dmin.shape), -1.0, 1.0) * dmin / P.dt
+        return np.ascontiguousarray(np.where(v > 0, rp[tuple(lo)], rp[tuple(hi)]) * v)
+
+    return faces(wx, P.rho, nx + 1, 1), faces(wy, P.rho, ny + 1, 0)
 
 
 CONFIGS = {0: config0, 1: config1, 2: config2}
