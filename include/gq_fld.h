@@ -232,6 +232,29 @@ typedef struct {
 
 gq_status gq_fld_precond_info(const gq_fld_plan *plan, gq_precond_info *out);
 
+/* Explicit radiation advection, Sec. 3.2.1 (Eq. adv, with g = dS / dV of Eq. fldg).
+ *
+ * gq_fld_adv_source writes S_adv [ny][nx] (device, erg cm^-3 s^-1) for the plan's grid:
+ * for each cell, the sum over its four faces of (A_face / V) f e_r, added on its lower
+ * faces (-x, -y) and subtracted on its upper ones, where
+ *   fx [ny][nx+1], fy [ny+1][nx]  device face mass fluxes (rho v from the hydro Riemann
+ *                                 solution), g cm^-2 s^-1, positive along +x / +y;
+ *   e_r = E_r / rho               of the upwind cell; a boundary face takes its one cell's.
+ * rho and E_r are device [ny][nx].  Enqueued on stream; nothing is checked on the device.
+ * Errors: GQ_ERR_INVALID_ARG (NULL pointer), GQ_ERR_CUDA (launch failed).
+ *
+ * gq_fld_set_source attaches S_adv (device [ny][nx], owned by the caller, which keeps it
+ * valid while attached; NULL detaches) to the plan.  Every later gq_fld_step and
+ * gq_fld_step_subcycled of this plan then adds S_adv dt to phi_11 (each sub-step adds
+ * S_adv times its own dt, so the hydro step receives S_adv dt_total, S_adv being
+ * computed once per hydro step from E^n as the paper's algorithm does).  A step whose
+ * E^n + S_adv dt is not positive in some cell returns GQ_ERR_INVALID_ARG (not finite:
+ * GQ_ERR_NONFINITE), fields unchanged.
+ * Batched, serving and allocation-free steps take no source. */
+gq_status gq_fld_adv_source(gq_fld_plan *plan, const double *rho, const double *E_r, const double *fx,
+                            const double *fy, double *S_adv, void *stream);
+gq_status gq_fld_set_source(gq_fld_plan *plan, const double *S_adv);
+
 /* Allocation-free single step (the paper has no counterpart).  For callers that cannot
  * allocate device memory: hosts whose device memory is fixed at start-up, plug-ins inside
  * another application's memory manager, loops that cannot afford the device

@@ -139,6 +139,8 @@ SIGNATURES = {
                                              ctypes.POINTER(SolverOpts), ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.POINTER(StepInfo)]),
     "gq_fld_precond_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(PrecondInfo)]),
+    "gq_fld_adv_source": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 5 + [ctypes.c_void_p]),
+    "gq_fld_set_source": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "gq_fld_step_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.POINTER(OpacityLaw), ctypes.POINTER(Eos), ctypes.c_double,

@@ -338,6 +338,7 @@ gq_status make_step_params(const gq_fld_plan* P, const double* rho, double* e_g,
     sp.E = E_r;
     sp.eg_out = e_g;
     sp.T_out = T_g_out;
+    sp.sadv = P->S_adv;
 
     SolveParams pp{};
     pp.nx = P->nx;
@@ -498,6 +499,26 @@ void gq_fld_destroy(gq_fld_plan* P) {
     for (int t = 0; t < 4; t++)
         if (P->ev[t]) cudaEventDestroy(P->ev[t]);
     delete P;
+}
+
+gq_status gq_fld_set_source(gq_fld_plan* P, const double* S_adv) {
+    if (!P) return GQ_ERR_INVALID_ARG;
+    P->S_adv = S_adv;
+    return GQ_OK;
+}
+
+gq_status gq_fld_adv_source(gq_fld_plan* P, const double* rho, const double* E_r, const double* fx,
+                            const double* fy, double* S_adv, void* stream) {
+    if (!P || !rho || !E_r || !fx || !fy || !S_adv) return GQ_ERR_INVALID_ARG;
+    cudaError_t e = cudaSetDevice(P->device);
+    if (e == cudaSuccess)
+        e = gq::launch_adv_source(P->nx, P->ny, P->geo, rho, E_r, fx, fy, S_adv, P->setup_blocks,
+                                  static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return GQ_ERR_CUDA;
+    }
+    return GQ_OK;
 }
 
 gq_status gq_fld_precond_info(const gq_fld_plan* P, gq_precond_info* out) {

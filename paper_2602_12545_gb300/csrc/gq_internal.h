@@ -165,6 +165,7 @@ struct StepParams {
     double *E;           // in E^n, out E^{n+1}
     double *eg_out;
     double *T_out;
+    const double *sadv;  // explicit radiation source S_adv per cell (Eq. adv), or null
 };
 
 struct SolveParams {
@@ -223,6 +224,8 @@ cudaError_t launch_setup(const StepParams& sp, const DeviceGeometry& g, const Wo
 cudaError_t launch_solve(const SolveParams& p, const Workspace& w, int grid, cudaStream_t st);
 cudaError_t launch_backsub(const StepParams& sp, const DeviceGeometry& g, const Workspace& w,
                            int setup_blocks, cudaStream_t st);
+cudaError_t launch_adv_source(int nx, int ny, const DeviceGeometry& g, const double* rho, const double* E,
+                              const double* fx, const double* fy, double* S, int nblk, cudaStream_t st);
 cudaError_t launch_face_flux(const StepParams& sp, const DeviceGeometry& g, const Workspace& w, double weight,
                              bool accumulate, double* Fx, double* Fy, int nblk, cudaStream_t st);
 int solve_max_blocks_per_sm();
@@ -262,4 +265,5 @@ struct gq_fld_plan {
     gq::SolveCtl* ctl_host;  // pinned
     cudaEvent_t ev[4];       // phase timing
     int last_precond;        // preconditioner of the last step (-1: none yet)
+    const double* S_adv;     // attached explicit radiation source (caller's device array) or null
 };

@@ -68,8 +68,10 @@ __device__ void cells_body(const StepParams& sp, const DeviceGeometry& g, const 
     int flags = 0;
     for (int k = blk * blockDim.x + threadIdx.x; k < sp.N; k += nblk * blockDim.x) {
         const double rho = sp.rho[k], e = sp.eg[k], E = sp.E[k];
-        if (!(isfinite(rho) && isfinite(e) && isfinite(E))) flags |= 2;
-        else if (!(rho > 0.0 && e > 0.0 && E > 0.0)) flags |= 1;
+        // E^n + S_adv dt: the explicit part of phi_11 (S_g = 0)
+        const double Ea = sp.sadv ? E + sp.dt * sp.sadv[k] : E;
+        if (!(isfinite(rho) && isfinite(e) && isfinite(E) && isfinite(Ea))) flags |= 2;
+        else if (!(rho > 0.0 && e > 0.0 && E > 0.0 && Ea > 0.0)) flags |= 1;
         const double V = g.V[k];
         const double cv = rho * sp.cvfac;
         const double T = e / cv;
@@ -85,7 +87,7 @@ __device__ void cells_body(const StepParams& sp, const DeviceGeometry& g, const 
         const double f = cv * ipsi;
         w.sig[k] = kR * rho;
         w.dloc[k] = V * (1.0 + beta * f);
-        w.rhs[k] = V * (E + beta * aT4 * f);
+        w.rhs[k] = V * (Ea + beta * aT4 * f);
         w.tA[k] = (e + 3.0 * beta * aT4) * ipsi;
         w.tB[k] = beta * ipsi;
         eloc += V * (E + e);
@@ -354,6 +356,50 @@ cudaError_t launch_batch_setup(const BatchArgs& a, int total, cudaStream_t st) {
 cudaError_t launch_batch_finish(const BatchArgs& a, int total, cudaStream_t st) {
     kb_backsub<<<total, kSetupThreads, 0, st>>>(a);
     kb_finalize<<<a.n, kSetupThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// Eq. adv: S_adv of each cell, sum over its four faces of +-(A / V) f e_r (lower faces
+// add, upper faces subtract) with e_r = E / rho of the upwind cell; a boundary face takes
+// its one cell's e_r.  A face's area is its geometric factor times its normal distance
+// (gx = A / dxf, gy = A / (ymet dyf)).
+__global__ void k_adv_source(int nx, int ny, DeviceGeometry g, const double* __restrict__ rho,
+                             const double* __restrict__ E, const double* __restrict__ fx,
+                             const double* __restrict__ fy, double* __restrict__ S) {
+    const int N = nx * ny;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+        const int j = k / nx, i = k - j * nx;
+        const double ek = E[k] / rho[k];
+        const int fw = j * (nx + 1) + i, fs = j * nx + i;
+        const double yw = g.ymet[i];
+        double s = 0.0;
+        {   // west (lower x)
+            const double f = fx[fw];
+            const double er = (f > 0.0 && i > 0) ? E[k - 1] / rho[k - 1] : ek;
+            s += g.gx[fw] * g.dxf[i] * f * er;
+        }
+        {   // east (upper x)
+            const double f = fx[fw + 1];
+            const double er = (f < 0.0 && i < nx - 1) ? E[k + 1] / rho[k + 1] : ek;
+            s -= g.gx[fw + 1] * g.dxf[i + 1] * f * er;
+        }
+        {   // south (lower y)
+            const double f = fy[fs];
+            const double er = (f > 0.0 && j > 0) ? E[k - nx] / rho[k - nx] : ek;
+            s += g.gy[fs] * (yw * g.dyf[j]) * f * er;
+        }
+        {   // north (upper y)
+            const double f = fy[fs + nx];
+            const double er = (f < 0.0 && j < ny - 1) ? E[k + nx] / rho[k + nx] : ek;
+            s -= g.gy[fs + nx] * (yw * g.dyf[j + 1]) * f * er;
+        }
+        S[k] = s / g.V[k];
+    }
+}
+
+cudaError_t launch_adv_source(int nx, int ny, const DeviceGeometry& g, const double* rho, const double* E,
+                              const double* fx, const double* fy, double* S, int nblk, cudaStream_t st) {
+    k_adv_source<<<nblk, kSetupThreads, 0, st>>>(nx, ny, g, rho, E, fx, fy, S);
     return cudaGetLastError();
 }
 

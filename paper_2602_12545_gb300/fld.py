@@ -90,6 +90,35 @@ class FLDPlan:
             raise N.GQError(rc, "gq_fld_precond_info")
         return out.as_dict()
 
+    def adv_source(self, rho: torch.Tensor, E_r: torch.Tensor, fx: torch.Tensor, fy: torch.Tensor,
+                   out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """gq_fld_adv_source (Eq. adv): S_adv [ny][nx] from the face mass fluxes fx [ny][nx+1],
+        fy [ny+1][nx] and the upwind E_r / rho, on the current stream."""
+        shapes = ((rho, self.ny * self.nx, "rho"), (E_r, self.ny * self.nx, "E_r"),
+                  (fx, self.ny * (self.nx + 1), "fx"), (fy, (self.ny + 1) * self.nx, "fy"))
+        for t, n, name in shapes:
+            if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous() or t.numel() != n:
+                raise ValueError(f"{name} must be a contiguous float64 CUDA tensor of {n} elements")
+        if out is None:
+            out = torch.empty((self.ny, self.nx), dtype=torch.float64, device=rho.device)
+        st = torch.cuda.current_stream(rho.device).cuda_stream
+        rc = N.load().gq_fld_adv_source(self._h, rho.data_ptr(), E_r.data_ptr(), fx.data_ptr(), fy.data_ptr(),
+                                        out.data_ptr(), ctypes.c_void_p(st))
+        if rc != N.GQ_OK:
+            raise N.GQError(rc, "gq_fld_adv_source")
+        return out
+
+    def set_source(self, S_adv: Optional[torch.Tensor]):
+        """gq_fld_set_source: attach S_adv [ny][nx] (float64 CUDA) to the plan's later steps,
+        or detach with None.  The plan keeps a reference while attached."""
+        if S_adv is not None and (S_adv.dtype != torch.float64 or not S_adv.is_cuda or not S_adv.is_contiguous()
+                                  or S_adv.numel() != self.nx * self.ny):
+            raise ValueError(f"S_adv must be a contiguous float64 CUDA tensor of {self.nx * self.ny} elements")
+        rc = N.load().gq_fld_set_source(self._h, S_adv.data_ptr() if S_adv is not None else None)
+        if rc != N.GQ_OK:
+            raise N.GQError(rc, "gq_fld_set_source")
+        self._source = S_adv
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             N.load().gq_fld_destroy(self._h)
@@ -170,6 +199,14 @@ def step_problem(plan: FLDPlan, p: FLDProblem, rho, e_g, E_r, T_out=None, *, pre
     n_sub >= 1 sub-cycles it (Eq. subtimesteps)."""
     opts = SolverOptions(prec=p.precision if prec is None else prec, limiter=p.limiter,
                          rtol=p.rtol if rtol is None else rtol, **kw)
+    if p.S_adv is not None:
+        # the problem's explicit source, attached for this step only
+        plan.set_source(torch.as_tensor(np.ascontiguousarray(p.S_adv, dtype=np.float64)).to(rho.device))
+        try:
+            return plan.step(rho, e_g, E_r, T_out, opacity_R=p.opacity_R, opacity_P=p.opacity_P, gamma=p.gamma,
+                             mu=p.mu, dt=p.dt, bc=p.bc, opts=opts, check=check, n_sub=n_sub, q_t=q_t, Fx=Fx, Fy=Fy)
+        finally:
+            plan.set_source(None)
     return plan.step(rho, e_g, E_r, T_out, opacity_R=p.opacity_R, opacity_P=p.opacity_P, gamma=p.gamma,
                      mu=p.mu, dt=p.dt, bc=p.bc, opts=opts, check=check, n_sub=n_sub, q_t=q_t, Fx=Fx, Fy=Fy)
 
