@@ -249,7 +249,8 @@ gq_status gq_fld_precond_info(const gq_fld_plan *plan, gq_precond_info *out);
  * S_adv times its own dt, so the hydro step receives S_adv dt_total, S_adv being
  * computed once per hydro step from E^n as the paper's algorithm does).  A step whose
  * E^n + S_adv dt is not positive in some cell returns GQ_ERR_INVALID_ARG (not finite:
- * GQ_ERR_NONFINITE), fields unchanged.
+ * GQ_ERR_NONFINITE), fields unchanged; in a sub-cycled step the test is made on each
+ * sub-step's E, which strong gas coupling can drop far below E^n within a sub-step.
  * Batched, serving and allocation-free steps take no source. */
 gq_status gq_fld_adv_source(gq_fld_plan *plan, const double *rho, const double *E_r, const double *fx,
                             const double *fy, double *S_adv, void *stream);
