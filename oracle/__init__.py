@@ -30,6 +30,7 @@ class _Problem(ctypes.Structure):
         ("kR", ctypes.c_double * 4), ("kP", ctypes.c_double * 4),
         ("gamma", ctypes.c_double), ("mu", ctypes.c_double), ("dt", ctypes.c_double),
         ("bc", ctypes.c_int * 4), ("limiter", ctypes.c_int), ("S_adv", _dp),
+        ("Gx_in", _dp), ("Gy_in", _dp),
     ]
 
 
@@ -73,7 +74,7 @@ def _i(a: np.ndarray):
 class _Bound:
     """Keeps the numpy arrays referenced by a _Problem alive."""
 
-    def __init__(self, prob, V=None, Ax=None, Ay=None):
+    def __init__(self, prob, V=None, Ax=None, Ay=None, G=None):
         self.arrs = [np.ascontiguousarray(prob.x_faces, dtype=np.float64),
                      np.ascontiguousarray(prob.y_faces, dtype=np.float64),
                      None if V is None else np.ascontiguousarray(V, dtype=np.float64),
@@ -84,7 +85,8 @@ class _Bound:
                      np.ascontiguousarray(prob.E_r, dtype=np.float64)]
         S_adv = getattr(prob, "S_adv", None)
         self.arrs.append(None if S_adv is None else np.ascontiguousarray(S_adv, dtype=np.float64).ravel())
-        xf, yf, V_, Ax_, Ay_, rho, eg, E, S = self.arrs
+        self.arrs += [None, None] if G is None else [np.ascontiguousarray(g, dtype=np.float64).ravel() for g in G]
+        xf, yf, V_, Ax_, Ay_, rho, eg, E, S, Gx, Gy = self.arrs
         s = _Problem()
         s.nx, s.ny, s.coord = prob.nx, prob.ny, int(prob.coord)
         s.xf, s.yf, s.V_in, s.Ax_in, s.Ay_in = _d(xf), _d(yf), _d(V_), _d(Ax_), _d(Ay_)
@@ -96,6 +98,7 @@ class _Bound:
         s.gamma, s.mu, s.dt = float(prob.gamma), float(prob.mu), float(prob.dt)
         s.limiter = int(prob.limiter)
         s.S_adv = _d(S)
+        s.Gx_in, s.Gy_in = _d(Gx), _d(Gy)
         self.s = s
 
     def ref(self):
@@ -204,15 +207,16 @@ def pcg(A, rhs, x0, tol=1e-15, maxit=1000000):
     return x, it.value, crit.value, rc
 
 
-def step(prob, method: str = "lu", tol: float = 1e-15, V=None, Ax=None, Ay=None) -> dict:
+def step(prob, method: str = "lu", tol: float = 1e-15, V=None, Ax=None, Ay=None, G=None) -> dict:
     """One implicit step.  method 'lu': banded LU on the reduced system; 'cg': Jacobi-PCG on
     the reduced system to the cell-wise relative residual tol; 'coupled': banded LU on the
-    paper-literal coupled system (accurate only for moderate coupling)."""
+    paper-literal coupled system (accurate only for moderate coupling).  G = (Gx, Gy): frozen
+    face conductances A D / d (face weights dt G instead of those of this state)."""
     nx, ny = prob.nx, prob.ny
     E = np.zeros((ny, nx)); T = np.zeros((ny, nx)); eg = np.zeros((ny, nx))
     info = np.zeros(5)
     Fx = np.zeros((ny, nx + 1)); Fy = np.zeros((ny + 1, nx))
-    b = _Bound(prob, V, Ax, Ay)
+    b = _Bound(prob, V, Ax, Ay, G)
     m = {"lu": 0, "cg": 1, "coupled": 2}[method]
     rc = lib().orc_step(b.ref(), m, float(tol), _d(E), _d(T), _d(eg), _d(info), _d(Fx), _d(Fy))
     if rc < 0:
@@ -232,21 +236,31 @@ def subcycle_dts(dt_total: float, n_sub: int, q_t: float) -> list:
     return [dt0 * q_t ** (i - 1) for i in range(1, n_sub + 1)]
 
 
-def step_subcycled(prob, n_sub: int, q_t: float, method: str = "lu", tol: float = 1e-15) -> dict:
+def step_subcycled(prob, n_sub: int, q_t: float, method: str = "lu", tol: float = 1e-15,
+                   freeze_D: bool = False) -> dict:
     """prob.dt split into n_sub implicit steps (Eq. subtimesteps), each taken from the state
-    the previous one left, so opacities, limiter and coefficients are re-evaluated.  Fx, Fy:
-    the radiative face flux of the hydro step, the sub-steps' post-step fluxes weighted by
-    dt_i / dt (so that dt times it is the energy each face carried)."""
+    the previous one left, so opacities, C_V and the linearisation are re-evaluated.  D
+    (with kappa_R rho and the limiter) is re-formed from each sub-step's state too, unless
+    freeze_D: then, in the order of the paper's radiation algorithm (alpha updated, D
+    kept), every sub-step uses the face conductances A D / d of the hydro step's start
+    with its own dt.  Fx, Fy: the radiative face flux of the hydro step, the sub-steps'
+    post-step fluxes weighted by dt_i / dt (so that dt times it is the energy each face
+    carried); with freeze_D this is D^n sum_i (dt_i / dt) (E_m - E_k)_i / d, the
+    accumulation of Sec. 3.2.1."""
     import copy
     P = copy.copy(prob)
     P.E_r = np.array(prob.E_r, dtype=np.float64, copy=True)
     P.e_g = np.array(prob.e_g, dtype=np.float64, copy=True)
     first, out, its = None, None, 0
+    G = None
+    if freeze_D:
+        w = faces(prob)
+        G = (w["wx"] / prob.dt, w["wy"] / prob.dt)
     Fx = np.zeros((prob.ny, prob.nx + 1))
     Fy = np.zeros((prob.ny + 1, prob.nx))
     for dt in subcycle_dts(prob.dt, n_sub, q_t):
         P.dt = dt
-        out = step(P, method, tol)
+        out = step(P, method, tol, G=G)
         if first is None:
             first = out
         P.E_r = out["E_r"].copy()

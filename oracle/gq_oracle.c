@@ -279,6 +279,21 @@ static int work_build(const orc_problem *P, orc_work *W)
             }
         }
     }
+    /* frozen conductances (the paper's sub-cycle order keeps D from the start of the hydro
+     * step and only updates alpha = dt / d): w = dt G, D = G d / A for the diagnostics and
+     * the flux */
+    if (P->Gx_in) {
+        for (size_t f = 0; f < (size_t)ny * (nx + 1); f++) {
+            W->wx[f] = P->dt * P->Gx_in[f];
+            W->Dx[f] = W->Ax[f] > 0.0 && W->dx[f] > 0.0 ? P->Gx_in[f] * W->dx[f] / W->Ax[f] : 0.0;
+        }
+    }
+    if (P->Gy_in) {
+        for (size_t f = 0; f < (size_t)(ny + 1) * nx; f++) {
+            W->wy[f] = P->dt * P->Gy_in[f];
+            W->Dy[f] = W->Ay[f] > 0.0 && W->dy[f] > 0.0 ? P->Gy_in[f] * W->dy[f] / W->Ay[f] : 0.0;
+        }
+    }
     return 0;
 }
 

@@ -33,6 +33,9 @@ typedef struct {
     int limiter;              /* 0 Levermore-Pomraning (rational), 1 Minerbo, 2 none (1/3) */
     const double *S_adv;      /* optional explicit radiation source [ny][nx] (NULL: none),
                                  erg cm^-3 s^-1: the S_adv of phi_11 (Eq. adv) */
+    const double *Gx_in, *Gy_in;  /* optional frozen face conductances A D / d per face,
+                                 [ny][nx+1] and [ny+1][nx] (NULL: formed from this state);
+                                 given, every face weight is dt G (Milne faces included) */
 } orc_problem;
 
 /* physical constants (CGS) */
