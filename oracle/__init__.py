@@ -31,6 +31,7 @@ class _Problem(ctypes.Structure):
         ("gamma", ctypes.c_double), ("mu", ctypes.c_double), ("dt", ctypes.c_double),
         ("bc", ctypes.c_int * 4), ("limiter", ctypes.c_int), ("S_adv", _dp),
         ("Gx_in", _dp), ("Gy_in", _dp),
+        ("eos_n", ctypes.c_int), ("eos_T", _dp), ("eos_u", _dp),
     ]
 
 
@@ -86,7 +87,9 @@ class _Bound:
         S_adv = getattr(prob, "S_adv", None)
         self.arrs.append(None if S_adv is None else np.ascontiguousarray(S_adv, dtype=np.float64).ravel())
         self.arrs += [None, None] if G is None else [np.ascontiguousarray(g, dtype=np.float64).ravel() for g in G]
-        xf, yf, V_, Ax_, Ay_, rho, eg, E, S, Gx, Gy = self.arrs
+        tab = getattr(prob, "eos_table", None)
+        self.arrs += [None, None] if tab is None else [np.ascontiguousarray(t, dtype=np.float64) for t in tab]
+        xf, yf, V_, Ax_, Ay_, rho, eg, E, S, Gx, Gy, eT, eu = self.arrs
         s = _Problem()
         s.nx, s.ny, s.coord = prob.nx, prob.ny, int(prob.coord)
         s.xf, s.yf, s.V_in, s.Ax_in, s.Ay_in = _d(xf), _d(yf), _d(V_), _d(Ax_), _d(Ay_)
@@ -99,6 +102,8 @@ class _Bound:
         s.limiter = int(prob.limiter)
         s.S_adv = _d(S)
         s.Gx_in, s.Gy_in = _d(Gx), _d(Gy)
+        s.eos_n = 0 if eT is None else int(eT.size)
+        s.eos_T, s.eos_u = _d(eT), _d(eu)
         self.s = s
 
     def ref(self):

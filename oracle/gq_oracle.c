@@ -43,6 +43,9 @@
  *   - Reflecting boundary: no flux through the face.
  *   - Eq. adv at a boundary face: the upwind e_r is that of the face's one cell (a
  *     zero-gradient ghost), whichever way the given mass flux points.
+ *   - Non-linear C_V (Sec. 3.2.1 computes C_V per cell before the coefficients): with a
+ *     table u(T) (piecewise linear), T^n inverts u = e_g / rho on the segment that holds
+ *     it and C_V = rho du/dT of that segment; e_g^{n+1} = e_g^n + C_V (T^{n+1} - T^n).
  *   - Spherical-polar (r, theta), axisymmetric, the common factor 2 pi dropped:
  *     V = (r+^3 - r-^3)/3 (cos th- - cos th+), A_r = r^2 (cos th- - cos th+),
  *     A_th = sin th (r+^2 - r-^2)/2; volume centres r_c = int r dV / int dV and
@@ -206,11 +209,22 @@ static int work_build(const orc_problem *P, orc_work *W)
 
     const double c = C_LIGHT;
     const double mH = orc_const_mH();
-    /* cells: ideal-gas C_V = rho k_B / ((gamma-1) mu m_H); T = e_g / C_V; opacities at T^n */
+    /* cells: ideal-gas C_V = rho k_B / ((gamma-1) mu m_H) and T = e_g / C_V, or the table's
+     * T(u) and C_V = rho du/dT on the segment holding u = e_g / rho; opacities at T^n */
+    if (P->eos_n == 1 || P->eos_n < 0) { work_free(W); return -1; }
     for (int k = 0; k < N; k++) {
         double rho = P->rho[k];
-        W->CV[k] = rho * K_BOLTZ / ((P->gamma - 1.0) * P->mu * mH);
-        W->T[k] = P->eg[k] / W->CV[k];
+        if (P->eos_n >= 2) {
+            double u = P->eg[k] / rho;
+            int s = 0;                          /* segment [s, s+1]: the last with u_s <= u */
+            while (s + 2 < P->eos_n && P->eos_u[s + 1] <= u) s++;
+            double slope = (P->eos_u[s + 1] - P->eos_u[s]) / (P->eos_T[s + 1] - P->eos_T[s]);
+            W->T[k] = P->eos_T[s] + (u - P->eos_u[s]) / slope;
+            W->CV[k] = rho * slope;
+        } else {
+            W->CV[k] = rho * K_BOLTZ / ((P->gamma - 1.0) * P->mu * mH);
+            W->T[k] = P->eg[k] / W->CV[k];
+        }
         double kR = opacity(P->kR, rho, W->T[k]);
         double kP = opacity(P->kP, rho, W->T[k]);
         W->sig[k] = kR * rho;

@@ -36,6 +36,9 @@ typedef struct {
     const double *Gx_in, *Gy_in;  /* optional frozen face conductances A D / d per face,
                                  [ny][nx+1] and [ny+1][nx] (NULL: formed from this state);
                                  given, every face weight is dt G (Milne faces included) */
+    int eos_n;                /* tabulated EoS: 0 = ideal gas (gamma, mu); else eos_n >= 2 points */
+    const double *eos_T, *eos_u;  /* increasing T (K) and specific internal energy u (erg/g);
+                                 u(T) piecewise linear, extended linearly past both ends */
 } orc_problem;
 
 /* physical constants (CGS) */

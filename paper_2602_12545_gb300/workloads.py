@@ -70,6 +70,7 @@ class FLDProblem:
     precision: int = PREC_FP64
     rtol: float = 1e-10
     S_adv: Optional[np.ndarray] = None   # [ny][nx] explicit radiation source, erg cm^-3 s^-1
+    eos_table: Optional[tuple] = None    # (T [K], u [erg/g]) increasing: tabulated u(T); None = ideal gas
 
     @property
     def nx(self) -> int:
@@ -247,6 +248,28 @@ def random_small(nx: int, ny: int, coord: int, bc, seed: int, limiter: int = LIM
         dt = 10.0 ** rng.uniform(3.0, 6.0)
     return _pack(f"small_{'cart' if coord == CARTESIAN else 'sph'}{nx}x{ny}_s{seed}", coord, xf, yf,
                  rho, T, Trad, dt, bc=tuple(bc), limiter=limiter)
+
+
+def hydrogen_like_table(n: int = 64, T_lo: float = 10.0, T_hi: float = 1e6):
+    """A stand-in for a hydrogen EoS table (the paper's Fig. of C_V / rho against T shows
+    a dissociation bump near 3e3 K and an ionisation bump near 1e4 K): the specific heat
+    c(T) = (k_B / m_H) [1.5 + 20 exp(-(lg T - 3.5)^2 / 0.045) + 60 exp(-(lg T - 4.1)^2 / 0.02)]
+    integrated (trapezoid, 50 sub-intervals per table interval) to u(T) at n log-spaced
+    temperatures.  Returns (T, u)."""
+    T = np.exp(np.linspace(math.log(T_lo), math.log(T_hi), n))
+    kB_mH = _KB / _MH
+
+    def c(t):
+        lg = np.log10(t)
+        return kB_mH * (1.5 + 20.0 * np.exp(-(lg - 3.5) ** 2 / 0.045) + 60.0 * np.exp(-(lg - 4.1) ** 2 / 0.02))
+
+    u = np.empty(n)
+    u[0] = kB_mH * 1.5 * T[0]
+    for i in range(1, n):
+        t = np.linspace(T[i - 1], T[i], 51)
+        ct = c(t)
+        u[i] = u[i - 1] + float(np.sum(0.5 * (ct[1:] + ct[:-1]) * np.diff(t)))
+    return T, u
 
 
 def advected_packet(nx: int = 1024, v: float = 1.8e5, sigma_R: float = 1e7, E0: float = 2e5, cfl: float = 1.0,
