@@ -3,7 +3,8 @@
 TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
 benchmark's CPU-baseline leg may import this package.  It is a plain, slow C
 implementation (``gq_oracle.c``) that shares no code with the CUDA library; this
-module only marshals numpy arrays into it.
+module marshals numpy arrays into it and strings its single steps into sub-cycled ones.
+``smr.py`` assembles the two-level (SMR) matrix of Sec. 3.2.2 with numpy and scipy.
 """
 from __future__ import annotations
 
