@@ -111,7 +111,13 @@ typedef struct { int side[4]; } gq_bc;
  *               applies no factor).
  *   mg_block_cells  multigrid levels of at most this many cells are processed by one
  *               block of the solve (the others wait), larger ones by all blocks with
- *               grid-wide barriers between passes (0 = default 1024; >= 0). */
+ *               grid-wide barriers between passes (0 = default 1024; >= 0).
+ *   subcycle_freeze_D  gq_fld_step_subcycled only.  1: every sub-step forms its face
+ *               coefficients (kappa_R rho, the limiter, Milne faces) from the hydro step's
+ *               start state E^n, T^n, with its own dt: the order of the radiation algorithm
+ *               of Sec. 3.2.1, which updates alpha and keeps D between sub-steps.  0
+ *               (default): each sub-step re-forms them from the state it starts from.
+ *               Other values: GQ_ERR_INVALID_ARG. */
 typedef struct {
     int prec;
     int limiter;
@@ -126,7 +132,8 @@ typedef struct {
     int mg_block_cells;
     double mg_omega;
     double mg_over;
-    int reserved[2];
+    int subcycle_freeze_D;
+    int reserved;
 } gq_solver_opts;
 
 /* Result of one step (host struct). */

@@ -49,7 +49,7 @@ class SolverOpts(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("inner_rtol", ctypes.c_double), ("max_refine", ctypes.c_int),
                 ("spin_limit", ctypes.c_int64), ("restart", ctypes.c_int), ("timing", ctypes.c_int),
                 ("precond", ctypes.c_int), ("mg_block_cells", ctypes.c_int), ("mg_omega", ctypes.c_double),
-                ("mg_over", ctypes.c_double), ("reserved", ctypes.c_int * 2)]
+                ("mg_over", ctypes.c_double), ("subcycle_freeze_D", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class StepInfo(ctypes.Structure):

@@ -318,6 +318,7 @@ gq_status make_step_params(const gq_fld_plan* P, const double* rho, double* e_g,
     const double over = opts.mg_over == 0.0 ? 1.5 : opts.mg_over;
     if (!(omega > 0.0 && omega <= 1.0) || !(over > 0.0 && over < 2.0)) return GQ_ERR_INVALID_ARG;
     if (opts.mg_block_cells < 0) return GQ_ERR_INVALID_ARG;
+    if (opts.subcycle_freeze_D != 0 && opts.subcycle_freeze_D != 1) return GQ_ERR_INVALID_ARG;
 
     StepParams sp{};
     sp.nx = P->nx;
@@ -339,6 +340,10 @@ gq_status make_step_params(const gq_fld_plan* P, const double* rho, double* e_g,
     sp.eg_out = e_g;
     sp.T_out = T_g_out;
     sp.sadv = P->S_adv;
+    if (P->frz_on) {
+        sp.sig_n = P->frz;
+        sp.E_n = P->frz + P->N;
+    }
 
     SolveParams pp{};
     pp.nx = P->nx;
@@ -495,6 +500,7 @@ size_t gq_fld_plan_bytes_for(int nx, int ny) {
 void gq_fld_destroy(gq_fld_plan* P) {
     if (!P) return;
     if (P->arena) cudaFree(P->arena);
+    if (P->frz) cudaFree(P->frz);
     if (P->ctl_host) cudaFreeHost(P->ctl_host);
     for (int t = 0; t < 4; t++)
         if (P->ev[t]) cudaEventDestroy(P->ev[t]);
@@ -634,12 +640,43 @@ gq_status gq_fld_step_subcycled(gq_fld_plan* P, const double* rho, double* e_g, 
     // Eq. subtimesteps; q_t = 1 is the limit of the formula (equal sub-steps)
     const double dt0 = q_t == 1.0 ? dt_total / n_sub : dt_total * (1.0 - q_t) / (1.0 - std::pow(q_t, n_sub));
     if (!(dt0 > 0.0) || !std::isfinite(dt0)) return GQ_ERR_INVALID_ARG;
+    if (opts && opts->subcycle_freeze_D != 0 && opts->subcycle_freeze_D != 1) return GQ_ERR_INVALID_ARG;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    // the order of the radiation algorithm: sigma^n and E^n of the hydro step's start form
+    // every sub-step's face coefficients (sub-step 1 forms them itself)
+    const bool freeze = opts && opts->subcycle_freeze_D == 1 && n_sub > 1;
+    if (freeze) {
+        if (!E_r) return GQ_ERR_INVALID_ARG;
+        if (!P->frz) {
+            if (cudaSetDevice(P->device) != cudaSuccess) return GQ_ERR_CUDA;
+            if (cudaMalloc(&P->frz, 2 * sizeof(double) * (size_t)P->N) != cudaSuccess) {
+                cudaGetLastError();
+                P->frz = nullptr;
+                return GQ_ERR_OOM;
+            }
+        }
+        if (cudaMemcpyAsync(P->frz + P->N, E_r, sizeof(double) * (size_t)P->N, cudaMemcpyDeviceToDevice, cs) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return GQ_ERR_CUDA;
+        }
+    }
     gq_step_info acc{};
     gq_status result = GQ_OK;
     for (int i = 0; i < n_sub; i++) {
         const double dt = q_t == 1.0 ? dt0 : dt0 * std::pow(q_t, i);
         gq_step_info si{};
+        P->frz_on = freeze && i > 0 ? 1 : 0;
         const gq_status s = gq_fld_step(P, rho, e_g, E_r, T_g_out, op, eos, dt, bc, opts, stream, &si);
+        if (freeze && i == 0 && (s == GQ_OK || s == GQ_ERR_NOT_CONVERGED)) {
+            // sigma^n as sub-step 1's set-up formed it
+            if (cudaMemcpyAsync(P->frz, P->ws.sig, sizeof(double) * (size_t)P->N, cudaMemcpyDeviceToDevice, cs) !=
+                cudaSuccess) {
+                cudaGetLastError();
+                result = GQ_ERR_CUDA;
+                break;
+            }
+        }
         if ((Fx || Fy) && (s == GQ_OK || s == GQ_ERR_NOT_CONVERGED)) {
             // this sub-step's flux, weighted by its share of the hydro step (the workspace
             // still holds its coefficients)
@@ -676,6 +713,7 @@ gq_status gq_fld_step_subcycled(gq_fld_plan* P, const double* rho, double* e_g, 
             break;
         }
     }
+    P->frz_on = 0;
     acc.t_iter_us = acc.iterations > 0 ? (float)(1e3 * (acc.t_solve_ms - acc.t_precond_ms) / acc.iterations) : 0.f;
     acc.status = result;
     if (info) *info = acc;

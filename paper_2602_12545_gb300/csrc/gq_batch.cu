@@ -272,6 +272,7 @@ gq_status fill_descs(gq_batch* B, const gq_batch_item* items) {
                                            &it.bc, &it.opts, &sp, &pp, nullptr);
         if (s != GQ_OK) return s;
         sp.sadv = nullptr;   // batched steps take no explicit source
+        sp.sig_n = sp.E_n = nullptr;
         d.sp = sp;
         d.g = P->geo;
         d.w = P->ws;

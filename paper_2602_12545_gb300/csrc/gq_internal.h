@@ -166,6 +166,8 @@ struct StepParams {
     double *eg_out;
     double *T_out;
     const double *sadv;  // explicit radiation source S_adv per cell (Eq. adv), or null
+    const double *sig_n, *E_n;  // sigma and E the face coefficients are formed from when
+                                // they are held over sub-steps, or null (this step's)
 };
 
 struct SolveParams {
@@ -266,4 +268,6 @@ struct gq_fld_plan {
     cudaEvent_t ev[4];       // phase timing
     int last_precond;        // preconditioner of the last step (-1: none yet)
     const double* S_adv;     // attached explicit radiation source (caller's device array) or null
+    double* frz;             // 2 N doubles: sigma^n, E^n of a sub-cycled step (allocated on first use)
+    int frz_on;              // 1 while a sub-cycled step forms its faces from frz
 };

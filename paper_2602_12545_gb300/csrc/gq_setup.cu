@@ -124,15 +124,19 @@ __device__ __forceinline__ double milne_weight(double s, double h, double geo, i
 // folded into the cell's diagonal)
 __device__ void faces_body(const StepParams& sp, const DeviceGeometry& g, const Workspace& w, int blk, int nblk) {
     const int nx = sp.nx, ny = sp.ny;
+    // sigma and E of the face coefficients: this step's, or those held from the start of
+    // a sub-cycled hydro step
+    const double* sg = sp.sig_n ? sp.sig_n : w.sig;
+    const double* Eh = sp.E_n ? sp.E_n : sp.E;
     for (int k = blk * blockDim.x + threadIdx.x; k < sp.N; k += nblk * blockDim.x) {
         const int j = k / nx, i = k - j * nx;
-        const double sk = w.sig[k], Ek = sp.E[k];
+        const double sk = sg[k], Ek = Eh[k];
         double ww = 0.0, ws = 0.0, wb = 0.0;
         if (i > 0)
-            ww = face_weight(w.sig[k - 1], sk, sp.E[k - 1], Ek, g.thx[i], g.dxf[i],
+            ww = face_weight(sg[k - 1], sk, Eh[k - 1], Ek, g.thx[i], g.dxf[i],
                              g.gx[j * (nx + 1) + i], sp.limiter, sp.dt);
         if (j > 0)
-            ws = face_weight(w.sig[k - nx], sk, sp.E[k - nx], Ek, g.thy[j], g.ymet[i] * g.dyf[j],
+            ws = face_weight(sg[k - nx], sk, Eh[k - nx], Ek, g.thy[j], g.ymet[i] * g.dyf[j],
                              g.gy[j * nx + i], sp.limiter, sp.dt);
         if (i == 0 && sp.bc[0] == 1) wb += milne_weight(sk, g.dxf[0], g.gx[j * (nx + 1)], sp.limiter, sp.dt);
         if (i == nx - 1 && sp.bc[1] == 1)
@@ -414,6 +418,7 @@ __global__ void k_face_flux(StepParams sp, DeviceGeometry g, Workspace w, double
     const long long nfx = (long long)ny * (nx + 1), nfy = (long long)(ny + 1) * nx;
     const double* E = sp.E;
     const double* s = w.dloc;
+    const double* sg = sp.sig_n ? sp.sig_n : w.sig;   // the sigma the Milne faces were formed with
     auto milne = [&](double sig, double h, double Ek) {
         const double kk = 2.0 / (3.0 * sig * h);
         return kC * limiter(sp.limiter, 1.5) / sig * Ek / (h * (1.0 + kk));
@@ -429,7 +434,7 @@ __global__ void k_face_flux(StepParams sp, DeviceGeometry g, Workspace w, double
                 if (gA > 0.0) F = w.wW[k] / (s[k] * s[k - 1]) / (sp.dt * gA) * (E[k - 1] - E[k]) / g.dxf[i];
             } else if (sp.bc[i == 0 ? 0 : 1] == GQ_BC_OUTFLOW_MILNE) {
                 const int k = j * nx + (i == 0 ? 0 : nx - 1);
-                F = (i == 0 ? -1.0 : 1.0) * milne(w.sig[k], g.dxf[i], E[k]);
+                F = (i == 0 ? -1.0 : 1.0) * milne(sg[k], g.dxf[i], E[k]);
             }
             if (Fx) Fx[t] = (accumulate ? Fx[t] : 0.0) + weight * F;
         } else {
@@ -442,7 +447,7 @@ __global__ void k_face_flux(StepParams sp, DeviceGeometry g, Workspace w, double
                     F = w.wS[k] / (s[k] * s[k - nx]) / (sp.dt * gA) * (E[k - nx] - E[k]) / (g.ymet[i] * g.dyf[j]);
             } else if (sp.bc[j == 0 ? 2 : 3] == GQ_BC_OUTFLOW_MILNE) {
                 const int k = j == 0 ? i : (ny - 1) * nx + i;
-                F = (j == 0 ? -1.0 : 1.0) * milne(w.sig[k], g.ymet[i] * g.dyf[j], E[k]);
+                F = (j == 0 ? -1.0 : 1.0) * milne(sg[k], g.ymet[i] * g.dyf[j], E[k]);
             }
             if (Fy) Fy[f] = (accumulate ? Fy[f] : 0.0) + weight * F;
         }

@@ -39,6 +39,7 @@ class SolverOptions:
     mg_omega: float = 0.0         # 0 = library default
     mg_over: float = 0.0
     mg_block_cells: int = 0       # 0 = library default
+    subcycle_freeze_D: int = 0    # sub-cycled steps: 1 = D from the hydro step's start (the paper's order)
 
     def to_c(self) -> N.SolverOpts:
         o = N.SolverOpts()
@@ -48,6 +49,7 @@ class SolverOptions:
         o.spin_limit, o.restart, o.timing = int(self.spin_limit), int(self.restart), int(self.timing)
         o.precond, o.mg_omega, o.mg_over = int(self.precond), float(self.mg_omega), float(self.mg_over)
         o.mg_block_cells = int(self.mg_block_cells)
+        o.subcycle_freeze_D = int(self.subcycle_freeze_D)
         return o
 
 
