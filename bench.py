@@ -193,7 +193,8 @@ def kernel_source_hash():
     a committed ncu figure stays attached to the code it was measured on."""
     import re
     h = hashlib.sha256()
-    for name in ("gq_pcg.cu", "gq_mg.cuh", "gq_amg.cuh", "gq_device.cuh", "gq_internal.h"):
+    for name in ("gq_pcg.cuh", "gq_pcg_mixed.cu", "gq_pcg_fp64.cu", "gq_pcg_batch.cu", "gq_mg.cuh", "gq_amg.cuh",
+                 "gq_device.cuh", "gq_internal.h"):
         with open(os.path.join(ROOT, "paper_2602_12545_gb300", "csrc", name)) as f:
             src = f.read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)

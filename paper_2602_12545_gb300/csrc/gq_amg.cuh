@@ -1,4 +1,4 @@
-// Classical algebraic multigrid preconditioner (included by gq_pcg.cu).
+// Classical algebraic multigrid preconditioner (included by gq_pcg.cuh).
 //
 // Why: with cell-by-cell random densities and temperatures the flux-limited face weights
 // w_f jump by many orders of magnitude between neighbouring faces, and where the time

@@ -1,4 +1,4 @@
-// Aggregation-multigrid preconditioned conjugate gradients (included by gq_pcg.cu).
+// Aggregation-multigrid preconditioned conjugate gradients (included by gq_pcg.cuh).
 //
 // Preconditioner: one V-cycle on a hierarchy of 2 x 2 aggregates.  Level 0 is the
 // Jacobi-scaled system A^ = S A S; level l+1 is the Galerkin product P^T A_l P of

@@ -33,6 +33,11 @@
 // Both paths end with GQ_ERR_NOT_CONVERGED (best iterate kept) when the true residual
 // has not improved by 10% in 6 consecutive checks spanning at least 32 iterations: the
 // FP64 rounding floor of the cell-wise criterion lies above rtol.
+// The solver is compiled in three translation units that each instantiate one kernel:
+// gq_pcg_mixed.cu (k_pcg<true>), gq_pcg_fp64.cu (k_pcg<false>, and the host launchers of
+// the single-problem solve) and gq_pcg_batch.cu (kb_pcg).
+#pragma once
+
 #include <type_traits>
 
 #include "gq_device.cuh"
@@ -727,72 +732,10 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_pcg(SolveParams P, Workspa
     pcg_solve<MIXED>(P, w, Team{static_cast<int>(blockIdx.x), static_cast<int>(gridDim.x)}, sh, msh);
 }
 
-// Batched persistent solve: the co-resident grid is split into teams; the leader block
-// of a team takes the next problem of the team's class from the class queue, the team
-// solves it, and repeats until the queue is empty.  Teams synchronise only among
-// themselves, so small problems (one-block teams) never touch an inter-block barrier.
-__global__ void __launch_bounds__(kSolveThreads, 1) kb_pcg(BatchArgs a) {
-    __shared__ RedShared sh;
-    __shared__ MGShared msh;
-    __shared__ int s_idx;
-    const int tm = a.block_team[blockIdx.x];
-    const Team team{static_cast<int>(blockIdx.x) - a.team_first[tm], a.team_size[tm]};
-    const int c = a.team_class[tm];
-    const int qlen = a.class_start[c + 1] - a.class_start[c];
-    unsigned* tbar = a.team_bar + tm;
-    while (true) {
-        if (team.rank == 0 && threadIdx.x == 0) a.team_slot[tm] = atomicAdd(a.queue_head + c, 1);
-        if (!team_barrier(tbar, team, a.spin_limit, a.abort_flag)) return;
-        if (threadIdx.x == 0) s_idx = __ldcg(a.team_slot + tm);
-        // every block of the team has read the slot before the leader may overwrite it
-        if (!team_barrier(tbar, team, a.spin_limit, a.abort_flag)) return;
-        const int idx = s_idx;
-        if (idx >= qlen) return;
-        const ProbDesc& d = a.desc[a.queue[a.class_start[c] + idx]];
-        const bool ok = d.sp.mixed ? pcg_solve_outlined<true>(d.solve, d.w, team, sh, msh)
-                                   : pcg_solve_outlined<false>(d.solve, d.w, team, sh, msh);
-        if (!ok) return;
-    }
-}
-
 }  // namespace
 
-int solve_max_blocks_per_sm() {
-    int a = 0, b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pcg<true>, kSolveThreads, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pcg<false>, kSolveThreads, 0);
-    return a < b ? a : b;
-}
-
-int batch_solve_max_blocks_per_sm() {
-    int a = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, kb_pcg, kSolveThreads, 0);
-    return a;
-}
-
-cudaError_t launch_batch_solve(const BatchArgs& a, int grid, cudaStream_t st) {
-    BatchArgs ac = a;
-    void* args[] = {&ac};
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(kSolveThreads);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelExC(&cfg, reinterpret_cast<const void*>(kb_pcg), args);
-}
-
-cudaError_t launch_solve(const SolveParams& p, const Workspace& w, int grid, cudaStream_t st) {
-    SolveParams pc = p;
-    Workspace wc = w;
-    void* args[] = {&pc, &wc};
-    const void* fn = p.mixed ? reinterpret_cast<const void*>(k_pcg<true>)
-                             : reinterpret_cast<const void*>(k_pcg<false>);
-    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kSolveThreads), args, 0, st);
-}
+// host-side handles of the single-problem kernels (each defined in its own unit)
+const void* solve_kernel_mixed();
+const void* solve_kernel_fp64();
 
 }  // namespace gq
