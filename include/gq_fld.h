@@ -66,8 +66,24 @@ typedef struct {
  * (Sec. 2 defines kappa_R and kappa_P; the paper tabulates them, a power law stands in). */
 typedef struct { double k0_R, k1_R, a_R, b_R, k0_P, k1_P, a_P, b_P; } gq_opacity_law;
 
-/* Ideal gas: e_g = C_V T with C_V = rho k_B / ((gamma - 1) mu m_H) (Sec. 3.2, C_V = de/dT). */
-typedef struct { double gamma, mu; } gq_eos;
+/* Equation of state.
+ * table_n = 0: ideal gas, e_g = C_V T with C_V = rho k_B / ((gamma - 1) mu m_H) (Sec. 3.2,
+ *   C_V = de/dT).
+ * table_n >= 2: a tabulated EoS for the non-linear C_V of Sec. 3.2.1.  table_T (K) and
+ *   table_u (specific internal energy, erg/g) are DEVICE arrays of table_n increasing
+ *   values, owned by the caller.  u(T) is piecewise linear and extended linearly past both
+ *   ends.  Per cell, T^n solves u(T) = e_g / rho on the last segment whose lower end is at
+ *   or below e_g / rho, and C_V = rho du/dT on that segment; e_g^{n+1} = e_g^n +
+ *   C_V (T^{n+1} - T^n).  gamma and mu must still be valid but are not used.  A segment
+ *   that does not increase makes the step return GQ_ERR_NONFINITE.  Single and
+ *   sub-cycled steps only: batched steps and server requests with a table return
+ *   GQ_ERR_INVALID_ARG.
+ * Other table_n, or a table with a NULL array: GQ_ERR_INVALID_ARG. */
+typedef struct {
+    double gamma, mu;
+    int table_n;
+    const double *table_T, *table_u;
+} gq_eos;
 
 /* Per-side boundary kind: GQ_BC_REFLECT (no flux) or GQ_BC_OUTFLOW_MILNE (Eq. milne). */
 typedef struct { int side[4]; } gq_bc;

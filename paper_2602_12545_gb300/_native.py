@@ -37,7 +37,8 @@ class OpacityLaw(ctypes.Structure):
 
 
 class Eos(ctypes.Structure):
-    _fields_ = [("gamma", ctypes.c_double), ("mu", ctypes.c_double)]
+    _fields_ = [("gamma", ctypes.c_double), ("mu", ctypes.c_double), ("table_n", ctypes.c_int),
+                ("table_T", ctypes.c_void_p), ("table_u", ctypes.c_void_p)]
 
 
 class Bc(ctypes.Structure):

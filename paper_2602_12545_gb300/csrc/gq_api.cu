@@ -302,6 +302,8 @@ gq_status make_step_params(const gq_fld_plan* P, const double* rho, double* e_g,
     const double kP[4] = {op->k0_P, op->k1_P, op->a_P, op->b_P};
     if (!finite_all(kR, 4) || !finite_all(kP, 4)) return GQ_ERR_INVALID_ARG;
     if (!(dt > 0.0) || !std::isfinite(dt)) return GQ_ERR_INVALID_ARG;
+    if (eos->table_n < 0 || eos->table_n == 1 || (eos->table_n >= 2 && (!eos->table_T || !eos->table_u)))
+        return GQ_ERR_INVALID_ARG;
     if (!(eos->gamma > 1.0) || !(eos->mu > 0.0) || !std::isfinite(eos->gamma) || !std::isfinite(eos->mu))
         return GQ_ERR_INVALID_ARG;
     for (int s = 0; s < 4; s++)
@@ -333,6 +335,9 @@ gq_status make_step_params(const gq_fld_plan* P, const double* rho, double* e_g,
         sp.kP[t] = kP[t];
     }
     sp.cvfac = kKB / ((eos->gamma - 1.0) * eos->mu * kMH);
+    sp.eos_n = eos->table_n;
+    sp.eos_T = eos->table_T;
+    sp.eos_u = eos->table_u;
     sp.dt = dt;
     sp.rho = rho;
     sp.eg = e_g;

@@ -271,6 +271,7 @@ gq_status fill_descs(gq_batch* B, const gq_batch_item* items) {
         gq_status s = gq::make_step_params(P, it.rho, it.e_g, it.E_r, it.T_g_out, &it.opacity, &it.eos, it.dt,
                                            &it.bc, &it.opts, &sp, &pp, nullptr);
         if (s != GQ_OK) return s;
+        if (sp.eos_n != 0) return GQ_ERR_INVALID_ARG;   // batched steps take no EoS table
         sp.sadv = nullptr;   // batched steps take no explicit source
         sp.sig_n = sp.E_n = nullptr;
         d.sp = sp;

@@ -159,7 +159,9 @@ struct StepParams {
     int limiter;
     int mixed;
     double kR[4], kP[4];
-    double cvfac;        // C_V / rho = k_B / ((gamma - 1) mu m_H)
+    double cvfac;        // C_V / rho = k_B / ((gamma - 1) mu m_H) (ideal gas)
+    int eos_n;           // tabulated EoS: number of points (0: ideal gas)
+    const double *eos_T, *eos_u;  // its temperatures and specific internal energies
     double dt;
     const double *rho, *eg;
     double *E;           // in E^n, out E^{n+1}

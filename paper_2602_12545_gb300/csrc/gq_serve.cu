@@ -176,6 +176,7 @@ gq_status gq_server_create(const gq_server_opts* opts, gq_server** out) {
 }
 
 gq_status gq_server_submit(gq_server* S, const gq_request* rq, int64_t* id_out) {
+    if (rq && rq->eos.table_n != 0) return GQ_ERR_INVALID_ARG;   // requests take no EoS table
     if (!S || !rq || !id_out) return GQ_ERR_INVALID_ARG;
     const gq_grid_desc& g = rq->grid;
     if (g.nx < 1 || g.ny < 1 || !g.x_faces || !g.y_faces || !rq->rho || !rq->e_g || !rq->E_r || rq->n_steps < 1)

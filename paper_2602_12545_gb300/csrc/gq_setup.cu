@@ -56,6 +56,31 @@ __device__ __forceinline__ double block_sum(double v) {
     return t;   // valid in thread 0
 }
 
+// T^n and C_V of a cell: the ideal gas (C_V = rho cvfac, T = e / C_V), or the tabulated
+// u(T) inverted on the last segment whose lower end is at or below u = e / rho
+// (C_V = rho du/dT there; the end segments extend the table)
+__device__ __forceinline__ void cell_eos(const StepParams& sp, double rho, double e, double& cv, double& T) {
+    if (sp.eos_n >= 2) {
+        const double u = e / rho;
+        int s = 0, a = 1, b = sp.eos_n - 2;
+        while (a <= b) {
+            const int m = (a + b) >> 1;
+            if (sp.eos_u[m] <= u) {
+                s = m;
+                a = m + 1;
+            } else {
+                b = m - 1;
+            }
+        }
+        const double slope = (sp.eos_u[s + 1] - sp.eos_u[s]) / (sp.eos_T[s + 1] - sp.eos_T[s]);
+        T = sp.eos_T[s] + (u - sp.eos_u[s]) / slope;
+        cv = rho * slope;
+    } else {
+        cv = rho * sp.cvfac;
+        T = e / cv;
+    }
+}
+
 }  // namespace
 
 // Each body below processes one problem with nblk blocks, this block being number blk;
@@ -73,8 +98,9 @@ __device__ void cells_body(const StepParams& sp, const DeviceGeometry& g, const 
         if (!(isfinite(rho) && isfinite(e) && isfinite(E) && isfinite(Ea))) flags |= 2;
         else if (!(rho > 0.0 && e > 0.0 && E > 0.0 && Ea > 0.0)) flags |= 1;
         const double V = g.V[k];
-        const double cv = rho * sp.cvfac;
-        const double T = e / cv;
+        double cv, T;
+        cell_eos(sp, rho, e, cv, T);
+        if (sp.eos_n >= 2 && !(cv > 0.0 && isfinite(cv) && isfinite(T))) flags |= 2;
         const double kR = opacity(sp.kR, rho, T);
         const bool same = sp.kP[0] == sp.kR[0] && sp.kP[1] == sp.kR[1] && sp.kP[2] == sp.kR[2] &&
                           sp.kP[3] == sp.kR[3];
@@ -223,8 +249,9 @@ __device__ void backsub_body(const StepParams& sp, const DeviceGeometry& g, cons
             const double En = w.dloc[k] * w.y[k];
             const double Tn = w.tA[k] + w.tB[k] * En;
             const double e = sp.eg[k];
-            const double cv = sp.rho[k] * sp.cvfac;
-            const double en = e + cv * (Tn - e / cv);
+            double cv, T0;
+            cell_eos(sp, sp.rho[k], e, cv, T0);
+            const double en = e + cv * (Tn - T0);
             sp.E[k] = En;
             sp.eg_out[k] = en;
             if (sp.T_out) sp.T_out[k] = Tn;

@@ -146,7 +146,7 @@ class FLDPlan:
              *, opacity_R: Sequence[float], opacity_P: Sequence[float], gamma: float, mu: float, dt: float,
              bc: Sequence[int], opts: SolverOptions, stream: Optional[torch.cuda.Stream] = None,
              check: bool = True, n_sub: int = 0, q_t: float = 1.0, Fx: Optional[torch.Tensor] = None,
-             Fy: Optional[torch.Tensor] = None) -> dict:
+             Fy: Optional[torch.Tensor] = None, eos_table=None) -> dict:
         """One implicit step; e_g and E_r are updated in place, T_out receives T_g^{n+1}.
         With n_sub >= 1, dt is split into n_sub geometric sub-steps of ratio q_t
         (gq_fld_step_subcycled); Fx [ny][nx+1] and Fy [ny+1][nx] (float64 CUDA tensors) then
@@ -157,6 +157,13 @@ class FLDPlan:
             self._check(T_out, "T_out")
         op = N.OpacityLaw(*[float(v) for v in tuple(opacity_R) + tuple(opacity_P)])
         eos = N.Eos(float(gamma), float(mu))
+        if eos_table is not None:
+            # a tabulated u(T): two float64 CUDA tensors of the same length (kept alive by the caller)
+            tT, tu = eos_table
+            if (tT.dtype != torch.float64 or tu.dtype != torch.float64 or not tT.is_cuda or not tu.is_cuda
+                    or not tT.is_contiguous() or not tu.is_contiguous() or tT.numel() != tu.numel()):
+                raise ValueError("eos_table must be two contiguous float64 CUDA tensors of one length")
+            eos.table_n, eos.table_T, eos.table_u = int(tT.numel()), tT.data_ptr(), tu.data_ptr()
         b = N.Bc()
         for i in range(4):
             b.side[i] = int(bc[i])
