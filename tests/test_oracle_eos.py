@@ -5,8 +5,13 @@ dissociation and an ionisation bump stands in):
 - a table sampled from the ideal gas reproduces the ideal-gas step;
 - without coupling (kappa_P = 0) T^n is the inverse of the table, as numpy's interp
   evaluates it, and e_g is kept;
+- the tangent C_V: over a step that keeps T inside one table segment, the returned
+  T^{n+1} and e^{n+1} lie on that segment of u(T), so T^{n+1} is numpy's interp of
+  e^{n+1} / rho (a secant or wrong-segment C_V breaks this);
 - one cell exchanging energy with radiation, sub-cycled, converges at first order to the
   exchange ODE  rho du/dt = c kappa_P rho (E - a T(u)^4) = -dE/dt  integrated by scipy.
+  This pins the table inversion and the exchange.  It does not pin C_V: C_V only
+  linearises within a sub-step, and T is re-derived from e at the next one.
 """
 import dataclasses
 
@@ -41,6 +46,25 @@ def test_uncoupled_temperature_inverts_the_table(orc):
     out = orc.step(P)
     assert np.allclose(out["T_g"], np.interp(e_g / P.rho, u_tab, T_tab), rtol=1e-12, atol=0)
     assert np.allclose(out["e_g"], e_g, rtol=1e-15, atol=0)
+
+
+def test_tangent_cv_keeps_the_state_on_the_table(orc):
+    T_tab, u_tab = W.hydrogen_like_table()
+    P = W.random_small(13, 9, W.CARTESIAN, (0, 1, 0, 0), 24)
+    rng = np.random.default_rng(25)
+    T0 = 10.0 ** rng.uniform(2.5, 5.0, P.E_r.shape)
+    e_g = P.rho * np.interp(T0, T_tab, u_tab)
+    E = A_RAD * T0 ** 4 * (1.0 + 0.05 * rng.standard_normal(T0.shape))   # near equilibrium: small steps
+    P = dataclasses.replace(P, e_g=e_g, E_r=E, eos_table=(T_tab, u_tab), dt=10.0)
+    out = orc.step(P)
+    seg0 = np.searchsorted(T_tab, T0)
+    seg1 = np.searchsorted(T_tab, out["T_g"])
+    same = seg0 == seg1
+    assert same.mean() > 0.5
+    moved = np.abs(out["T_g"] / T0 - 1.0)
+    assert moved[same].max() > 1e-6             # the step does change T
+    back = np.interp(out["e_g"] / P.rho, u_tab, T_tab)
+    assert np.allclose(out["T_g"][same], back[same], rtol=1e-10, atol=0)
 
 
 def _one_cell(T_g, T_rad, rho, kP, dt, table):
