@@ -128,11 +128,11 @@ typedef struct { int side[4]; } gq_bc;
  *   mg_block_cells  multigrid levels of at most this many cells are processed by one
  *               block of the solve (the others wait), larger ones by all blocks with
  *               grid-wide barriers between passes (0 = default 1024; >= 0).
- *   subcycle_freeze_D  gq_fld_step_subcycled only.  1: every sub-step forms its face
- *               coefficients (kappa_R rho, the limiter, Milne faces) from the hydro step's
- *               start state E^n, T^n, with its own dt: the order of the radiation algorithm
- *               of Sec. 3.2.1, which updates alpha and keeps D between sub-steps.  0
- *               (default): each sub-step re-forms them from the state it starts from.
+ *   subcycle_freeze_D  gq_fld_step_subcycled only.  1 (default): every sub-step forms its
+ *               face coefficients (kappa_R rho, the limiter, Milne faces) from the hydro
+ *               step's start state E^n, T^n, with its own dt: the order of the radiation
+ *               algorithm of Sec. 3.2.1, which updates alpha and keeps D between sub-steps.
+ *               0: each sub-step re-forms them from the state it starts from.
  *               Other values: GQ_ERR_INVALID_ARG. */
 typedef struct {
     int prec;
@@ -206,7 +206,10 @@ gq_status gq_fld_step(gq_fld_plan *plan, const double *rho, double *e_g, double 
  * length (Sec. 3.2, Eq. subtimesteps): dt_i = dt_0 q_t^(i-1), i = 1..n_sub, with
  * dt_0 = dt_total (1 - q_t) / (1 - q_t^n_sub), so that they add up to dt_total (q_t = 1:
  * equal sub-steps).  Each sub-step is gq_fld_step from the state the previous one left,
- * so opacities, limiter and coefficients are re-evaluated.  Arguments as gq_fld_step;
+ * so C_V, the Planck opacity and the linearisation are re-evaluated; the face
+ * coefficients (kappa_R rho, the limiter, D) are held from the hydro step's start
+ * (opts->subcycle_freeze_D = 1, the default: the order of the radiation algorithm of
+ * Sec. 3.2.1) or re-formed per sub-step (0).  Arguments as gq_fld_step;
  * n_sub >= 1, q_t > 0 (the paper uses 1 < q_t < 2), dt_total > 0.  info: iterations and
  * refinements summed, residuals the largest of the sub-steps, energy_before of the first
  * and energy_after of the last sub-step, timings summed.  A sub-step that ends with
@@ -214,7 +217,7 @@ gq_status gq_fld_step(gq_fld_plan *plan, const double *rho, double *e_g, double 
  * any other error stops it and is returned.
  *   Fx, Fy   [ny][nx+1], [ny+1][nx] device (each may be NULL): the radiative flux of the
  *            hydro step through every face, erg cm^-2 s^-1, positive along +x / +y: the
- *            sub-steps' fluxes -D grad E (their own D, and E after the sub-step) weighted
+ *            sub-steps' fluxes -D grad E (the D they were solved with, and E after the sub-step) weighted
  *            by dt_i / dt_total, so that dt_total times it is the energy the face carried
  *            (the accumulation of Sec. 3.2.1).  Reflecting faces carry 0; Milne faces
  *            D_b E / (h (1 + k)) outward. */
@@ -288,11 +291,15 @@ gq_status gq_fld_set_source(gq_fld_plan *plan, const double *S_adv);
  * makes no cudaMalloc / cudaFree / allocating call.  The caller passes inputs and outputs:
  * x_faces (nx+1) and y_faces (ny+1) as DEVICE arrays, the fields as in gq_fld_step (no
  * explicit areas or volumes).  Grids whose footprint exceeds the array (about 50 000 cells)
- * return GQ_ERR_INVALID_ARG before any work.  All calls on a device share the array and it
- * keeps the previous call's contents; the call resets what must start at zero, and calls
+ * return GQ_ERR_INVALID_ARG before any work.  The faces are checked on the device as
+ * gq_fld_setup checks them on the host (finite, strictly increasing, r > 0 and theta in
+ * [0, pi] for spherical-polar grids, positive volumes): a violation returns
+ * GQ_ERR_INVALID_ARG with the fields untouched.  All calls on a device share the array and
+ * it keeps the previous call's contents; the call resets what must start at zero, and calls
  * that overlap on the GPU (other streams or host threads) race: serialise them.  The first
  * call on a device looks up the array's device address (cudaGetSymbolAddress); make that
- * first call before any stream capture.  info->t_*_ms are not filled. */
+ * first call before any stream capture.  Every call synchronises with its stream before
+ * returning (it reads the step's status back).  info->t_*_ms are not filled. */
 gq_status gq_fld_step_noalloc(int nx, int ny, int coord, const double *x_faces, const double *y_faces,
                               const double *rho, double *e_g, double *E_r, double *T_g_out,
                               const gq_opacity_law *opacity, const gq_eos *eos, double dt, const gq_bc *bc,
@@ -454,7 +461,8 @@ void gq_server_destroy(gq_server *server);
 
 /* Default solver options: FP64, LP limiter, rtol 1e-10, max_iter 200000, inner_rtol 0.1,
  * max_refine 200, default spin limit, keep the search direction, algebraic multigrid
- * preconditioning (omega 0.8; coarse factor 1.5 for the aggregation cycle). */
+ * preconditioning (omega 0.8; coarse factor 1.5 for the aggregation cycle), sub-cycled
+ * steps in the paper's order (subcycle_freeze_D = 1). */
 void gq_solver_opts_default(gq_solver_opts *opts);
 
 /* Static description of a status code. */

@@ -243,13 +243,13 @@ def subcycle_dts(dt_total: float, n_sub: int, q_t: float) -> list:
 
 
 def step_subcycled(prob, n_sub: int, q_t: float, method: str = "lu", tol: float = 1e-15,
-                   freeze_D: bool = False) -> dict:
+                   freeze_D: bool = True) -> dict:
     """prob.dt split into n_sub implicit steps (Eq. subtimesteps), each taken from the state
-    the previous one left, so opacities, C_V and the linearisation are re-evaluated.  D
-    (with kappa_R rho and the limiter) is re-formed from each sub-step's state too, unless
-    freeze_D: then, in the order of the paper's radiation algorithm (alpha updated, D
-    kept), every sub-step uses the face conductances A D / d of the hydro step's start
-    with its own dt.  Fx, Fy: the radiative face flux of the hydro step, the sub-steps'
+    the previous one left, so opacities, C_V and the linearisation are re-evaluated.  With
+    freeze_D (the default), in the order of the paper's radiation algorithm (alpha updated,
+    D kept), every sub-step uses the face conductances A D / d of the hydro step's start
+    with its own dt; without it, D (with kappa_R rho and the limiter) is re-formed from
+    each sub-step's state too.  Fx, Fy: the radiative face flux of the hydro step, the sub-steps'
     post-step fluxes weighted by dt_i / dt (so that dt times it is the energy each face
     carried); with freeze_D this is D^n sum_i (dt_i / dt) (E_m - E_k)_i / d, the
     accumulation of Sec. 3.2.1."""

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "gq_device.cuh"
+#include "gq_geometry.cuh"
 #include "gq_internal.h"
 
 namespace {
@@ -15,24 +16,6 @@ namespace {
 // ---------------------------------------------------------------------------
 // host geometry (FP64): volumes, face areas, volume centres, centre distances
 // ---------------------------------------------------------------------------
-
-// int_{v}^{v+h} (t - v) sin t dt and int_v^{v+h} sin t dt, evaluated without
-// cancellation for small h (series in h for the two h-only factors).
-void theta_moments(double v, double h, double* first, double* zeroth) {
-    double A, B;   // A = cos h + h sin h - 1, B = sin h - h cos h
-    if (h < 0.05) {
-        const double h2 = h * h;
-        A = h2 * (0.5 + h2 * (-1.0 / 8.0 + h2 * (1.0 / 144.0 + h2 * (-1.0 / 5760.0))));
-        B = h2 * h * (1.0 / 3.0 + h2 * (-1.0 / 30.0 + h2 * (1.0 / 840.0 + h2 * (-1.0 / 45360.0))));
-    } else {
-        A = std::cos(h) + h * std::sin(h) - 1.0;
-        B = std::sin(h) - h * std::cos(h);
-    }
-    const double sv = std::sin(v), cv = std::cos(v);
-    const double half = std::sin(0.5 * h);
-    *first = sv * A + cv * B;
-    *zeroth = sv * std::sin(h) + cv * 2.0 * half * half;
-}
 
 struct HostGeometry {
     std::vector<double> V, gx, gy, dxf, thx, ymet, dyf, thy;
@@ -50,42 +33,20 @@ gq_status build_geometry(const gq_grid_desc* gd, HostGeometry& H) {
     if (sph && (!(xf[0] > 0.0) || yf[0] < 0.0 || yf[ny] > M_PI + 1e-12)) return GQ_ERR_INVALID_ARG;
 
     std::vector<double> xc(nx), yc(ny), dcos(ny);
-    if (!sph) {
-        for (int i = 0; i < nx; i++) xc[i] = 0.5 * (xf[i] + xf[i + 1]);
-        for (int j = 0; j < ny; j++) yc[j] = 0.5 * (yf[j] + yf[j + 1]);
-    } else {
-        for (int i = 0; i < nx; i++) {
-            const double a = xf[i], b = xf[i + 1];
-            // int r^3 dr / int r^2 dr over [a, b]
-            xc[i] = 0.75 * (a + b) * (a * a + b * b) / (a * a + a * b + b * b);
-        }
-        for (int j = 0; j < ny; j++) {
-            double m1, m0;
-            theta_moments(yf[j], yf[j + 1] - yf[j], &m1, &m0);
-            yc[j] = yf[j] + m1 / m0;
-            dcos[j] = m0;
-        }
-    }
+    for (int i = 0; i < nx; i++) xc[i] = gq::geom::x_centre(xf[i], xf[i + 1], sph);
+    for (int j = 0; j < ny; j++) yc[j] = gq::geom::y_centre(yf[j], yf[j + 1], sph, &dcos[j]);
     const size_t N = (size_t)nx * ny;
     H.V.assign(N, 0.0);
     std::vector<double> Ax((size_t)ny * (nx + 1)), Ay((size_t)(ny + 1) * nx);
     for (int j = 0; j < ny; j++)
-        for (int i = 0; i < nx; i++) {
-            const double a = xf[i], b = xf[i + 1];
-            H.V[(size_t)j * nx + i] = sph ? (b - a) * (a * a + a * b + b * b) / 3.0 * dcos[j]
-                                          : (b - a) * (yf[j + 1] - yf[j]);
-        }
+        for (int i = 0; i < nx; i++)
+            H.V[(size_t)j * nx + i] = gq::geom::cell_volume(xf[i], xf[i + 1], yf[j], yf[j + 1], sph, dcos[j]);
     for (int j = 0; j < ny; j++)
         for (int i = 0; i <= nx; i++)
-            Ax[(size_t)j * (nx + 1) + i] = sph ? xf[i] * xf[i] * dcos[j] : yf[j + 1] - yf[j];
-    for (int j = 0; j <= ny; j++) {
-        double sf = 1.0;
-        if (sph) sf = (yf[j] <= 0.0 || yf[j] >= M_PI) ? 0.0 : std::sin(yf[j]);
-        for (int i = 0; i < nx; i++) {
-            const double a = xf[i], b = xf[i + 1];
-            Ay[(size_t)j * nx + i] = sph ? sf * (b - a) * (b + a) * 0.5 : b - a;
-        }
-    }
+            Ax[(size_t)j * (nx + 1) + i] = gq::geom::x_face_area(xf[i], yf[j], yf[j + 1], sph, dcos[j]);
+    for (int j = 0; j <= ny; j++)
+        for (int i = 0; i < nx; i++)
+            Ay[(size_t)j * nx + i] = gq::geom::y_face_area(yf[j], xf[i], xf[i + 1], sph);
     if (gd->volume) std::memcpy(H.V.data(), gd->volume, sizeof(double) * N);
     if (gd->area_x) std::memcpy(Ax.data(), gd->area_x, sizeof(double) * Ax.size());
     if (gd->area_y) std::memcpy(Ay.data(), gd->area_y, sizeof(double) * Ay.size());
@@ -427,6 +388,7 @@ void gq_solver_opts_default(gq_solver_opts* o) {
     o->precond = GQ_PRECOND_AMG;
     o->mg_omega = 0.8;
     o->mg_over = 1.5;
+    o->subcycle_freeze_D = 1;
 }
 
 gq_status gq_fld_setup(const gq_grid_desc* gd, gq_fld_plan** out) {
@@ -645,11 +607,12 @@ gq_status gq_fld_step_subcycled(gq_fld_plan* P, const double* rho, double* e_g, 
     // Eq. subtimesteps; q_t = 1 is the limit of the formula (equal sub-steps)
     const double dt0 = q_t == 1.0 ? dt_total / n_sub : dt_total * (1.0 - q_t) / (1.0 - std::pow(q_t, n_sub));
     if (!(dt0 > 0.0) || !std::isfinite(dt0)) return GQ_ERR_INVALID_ARG;
-    if (opts && opts->subcycle_freeze_D != 0 && opts->subcycle_freeze_D != 1) return GQ_ERR_INVALID_ARG;
+    const int freeze_D = opts ? opts->subcycle_freeze_D : 1;      // NULL options: the defaults
+    if (freeze_D != 0 && freeze_D != 1) return GQ_ERR_INVALID_ARG;
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     // the order of the radiation algorithm: sigma^n and E^n of the hydro step's start form
     // every sub-step's face coefficients (sub-step 1 forms them itself)
-    const bool freeze = opts && opts->subcycle_freeze_D == 1 && n_sub > 1;
+    const bool freeze = freeze_D == 1 && n_sub > 1;
     if (freeze) {
         if (!E_r) return GQ_ERR_INVALID_ARG;
         if (!P->frz) {

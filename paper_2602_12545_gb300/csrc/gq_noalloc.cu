@@ -19,10 +19,16 @@
 //   - The first call on a device resolves the array's device address with
 //     cudaGetSymbolAddress (host code cannot use the symbol itself as a device pointer:
 //     it names a host-side shadow).  Make that first call before any stream capture.
+//   - Every call synchronises with its stream before it returns: it reads the step's
+//     status back into host memory.
+//   - The face coordinates come from the caller's device memory, so they are checked on
+//     the device (see k_geo1d); a grid gq_fld_setup would reject returns
+//     GQ_ERR_INVALID_ARG here too, with the fields untouched.
 #include <cstring>
 #include <mutex>
 
 #include "gq_device.cuh"
+#include "gq_geometry.cuh"
 #include "gq_internal.h"
 
 namespace gq {
@@ -50,101 +56,90 @@ cudaError_t scratch_address(int dev, void** out) {
     return cudaSuccess;
 }
 
-// theta moments as in the plan's host geometry, on the device
-__device__ void theta_moments_dev(double v, double h, double* first, double* zeroth) {
-    double A, B;
-    if (h < 0.05) {
-        const double h2 = h * h;
-        A = h2 * (0.5 + h2 * (-1.0 / 8.0 + h2 * (1.0 / 144.0 + h2 * (-1.0 / 5760.0))));
-        B = h2 * h * (1.0 / 3.0 + h2 * (-1.0 / 30.0 + h2 * (1.0 / 840.0 + h2 * (-1.0 / 45360.0))));
-    } else {
-        A = cos(h) + h * sin(h) - 1.0;
-        B = sin(h) - h * cos(h);
-    }
-    const double sv = sin(v), cv = cos(v), half = sin(0.5 * h);
-    *first = sv * A + cv * B;
-    *zeroth = sv * sin(h) + cv * 2.0 * half * half;
-}
+// The geometry formulas are gq_geometry.cuh's, which the plan's host set-up uses too.
+// Caller-supplied faces are validated here as gq_fld_setup validates them on the host:
+// finite and strictly increasing, r > 0 and theta within [0, pi] for spherical-polar
+// grids, every volume positive and finite.  A violation sets bit 0 of the control
+// block's input flags, so the solve does not run, the fields are left as they were and
+// the call returns GQ_ERR_INVALID_ARG.
 
-__device__ double xcen(const double* xf, int i, bool sph) {
-    const double a = xf[i], b = xf[i + 1];
-    return sph ? 0.75 * (a + b) * (a * a + b * b) / (a * a + a * b + b * b) : 0.5 * (a + b);
-}
-
-__device__ double ycen(const double* yf, int j, bool sph, double* dcos) {
-    if (!sph) {
-        *dcos = 1.0;
-        return 0.5 * (yf[j] + yf[j + 1]);
-    }
-    double m1, m0;
-    theta_moments_dev(yf[j], yf[j + 1] - yf[j], &m1, &m0);
-    *dcos = m0;
-    return yf[j] + m1 / m0;
-}
-
-// 1-D geometry: dxf, thx, ymet (x-direction), dyf, thy (y-direction)
-__global__ void k_geo1d(int nx, int ny, int sph, const double* xf, const double* yf, DeviceGeometry g) {
+// 1-D geometry: dxf, thx, ymet (x-direction), dyf, thy (y-direction), and the face checks
+__global__ void k_geo1d(int nx, int ny, int sph, const double* xf, const double* yf, DeviceGeometry g,
+                        int* input_flags) {
     double* dxf = const_cast<double*>(g.dxf);
     double* thx = const_cast<double*>(g.thx);
     double* ymet = const_cast<double*>(g.ymet);
     double* dyf = const_cast<double*>(g.dyf);
     double* thy = const_cast<double*>(g.thy);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    bool bad = false;
     if (t <= nx) {
         const int i = t;
-        if (i == 0) { dxf[0] = xcen(xf, 0, sph) - xf[0]; thx[0] = 0.0; }
-        else if (i == nx) { dxf[nx] = xf[nx] - xcen(xf, nx - 1, sph); thx[nx] = 0.0; }
-        else {
-            const double a = xcen(xf, i - 1, sph), b = xcen(xf, i, sph);
+        bad |= !isfinite(xf[i]) || (i > 0 && !(xf[i] > xf[i - 1])) || (sph && i == 0 && !(xf[0] > 0.0));
+        if (i == 0) {
+            dxf[0] = geom::x_centre(xf[0], xf[1], sph) - xf[0];
+            thx[0] = 0.0;
+        } else if (i == nx) {
+            dxf[nx] = xf[nx] - geom::x_centre(xf[nx - 1], xf[nx], sph);
+            thx[nx] = 0.0;
+        } else {
+            const double a = geom::x_centre(xf[i - 1], xf[i], sph), b = geom::x_centre(xf[i], xf[i + 1], sph);
             dxf[i] = b - a;
             thx[i] = (xf[i] - a) / (b - a);
         }
-        if (i < nx) ymet[i] = sph ? xcen(xf, i, sph) : 1.0;
+        if (i < nx) ymet[i] = sph ? geom::x_centre(xf[i], xf[i + 1], sph) : 1.0;
     }
     if (t <= ny) {
         const int j = t;
+        bad |= !isfinite(yf[j]) || (j > 0 && !(yf[j] > yf[j - 1]));
+        if (sph) bad |= (j == 0 && yf[0] < 0.0) || (j == ny && yf[ny] > geom::kPi + 1e-12);
         double dc;
-        if (j == 0) { dyf[0] = ycen(yf, 0, sph, &dc) - yf[0]; thy[0] = 0.0; }
-        else if (j == ny) { dyf[ny] = yf[ny] - ycen(yf, ny - 1, sph, &dc); thy[ny] = 0.0; }
-        else {
-            const double a = ycen(yf, j - 1, sph, &dc), b = ycen(yf, j, sph, &dc);
+        if (j == 0) {
+            dyf[0] = geom::y_centre(yf[0], yf[1], sph, &dc) - yf[0];
+            thy[0] = 0.0;
+        } else if (j == ny) {
+            dyf[ny] = yf[ny] - geom::y_centre(yf[ny - 1], yf[ny], sph, &dc);
+            thy[ny] = 0.0;
+        } else {
+            const double a = geom::y_centre(yf[j - 1], yf[j], sph, &dc), b = geom::y_centre(yf[j], yf[j + 1], sph, &dc);
             dyf[j] = b - a;
             thy[j] = (yf[j] - a) / (b - a);
         }
     }
+    if (bad) atomicOr(input_flags, 1);
 }
 
-// 2-D geometry: V per cell, A/d per x-face and y-face (uses the 1-D arrays)
-__global__ void k_geo2d(int nx, int ny, int sph, const double* xf, const double* yf, DeviceGeometry g) {
+// 2-D geometry: V per cell (checked positive and finite), A/d per x-face and y-face (uses
+// the 1-D arrays)
+__global__ void k_geo2d(int nx, int ny, int sph, const double* xf, const double* yf, DeviceGeometry g,
+                        int* input_flags) {
     double* V = const_cast<double*>(g.V);
     double* gx = const_cast<double*>(g.gx);
     double* gy = const_cast<double*>(g.gy);
     const long long nxf = (long long)ny * (nx + 1), nyf = (long long)(ny + 1) * nx, N = (long long)nx * ny;
+    bool bad = false;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N + nxf + nyf;
          t += (long long)gridDim.x * blockDim.x) {
         if (t < N) {
             const int j = (int)(t / nx), i = (int)(t - (long long)j * nx);
-            const double a = xf[i], b = xf[i + 1];
-            double dc = 1.0;
-            if (sph) ycen(yf, j, true, &dc);
-            V[t] = sph ? (b - a) * (a * a + a * b + b * b) / 3.0 * dc : (b - a) * (yf[j + 1] - yf[j]);
+            double dc;
+            geom::y_centre(yf[j], yf[j + 1], sph, &dc);
+            const double v = geom::cell_volume(xf[i], xf[i + 1], yf[j], yf[j + 1], sph, dc);
+            bad |= !(v > 0.0) || !isfinite(v);
+            V[t] = v;
         } else if (t < N + nxf) {
             const long long f = t - N;
             const int j = (int)(f / (nx + 1)), i = (int)(f - (long long)j * (nx + 1));
-            double dc = 1.0;
-            if (sph) ycen(yf, j, true, &dc);
-            const double A = sph ? xf[i] * xf[i] * dc : yf[j + 1] - yf[j];
-            gx[f] = A / g.dxf[i];
+            double dc;
+            geom::y_centre(yf[j], yf[j + 1], sph, &dc);
+            gx[f] = geom::x_face_area(xf[i], yf[j], yf[j + 1], sph, dc) / g.dxf[i];
         } else {
             const long long f = t - N - nxf;
             const int j = (int)(f / nx), i = (int)(f - (long long)j * nx);
-            double sf = 1.0;
-            if (sph) sf = (yf[j] <= 0.0 || yf[j] >= M_PI) ? 0.0 : sin(yf[j]);
-            const double a = xf[i], b = xf[i + 1];
-            const double A = sph ? sf * (b - a) * (b + a) * 0.5 : b - a;
-            gy[f] = A / (g.ymet[i] * g.dyf[j]);
+            gy[f] = geom::y_face_area(yf[j], xf[i], xf[i + 1], sph) / (g.ymet[i] * g.dyf[j]);
         }
     }
+    if (bad) atomicOr(input_flags, 1);
 }
 
 }  // namespace
@@ -197,13 +192,16 @@ gq_status gq_fld_step_noalloc(int nx, int ny, int coord, const double* x_faces, 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int sph = coord == GQ_SPHERICAL_POLAR;
     const int n1 = std::max(nx, ny) + 1;
-    gq::k_geo1d<<<(n1 + 255) / 256, 256, 0, st>>>(nx, ny, sph, x_faces, y_faces, P.geo);
-    gq::k_geo2d<<<std::max(1, std::min(sms * 8, (int)((3ll * P.N + 255) / 256))), 256, 0, st>>>(
-        nx, ny, sph, x_faces, y_faces, P.geo);
-    cudaError_t e = cudaGetLastError();
-    // the control block and the barrier word must start at zero
-    if (e == cudaSuccess) e = cudaMemsetAsync(P.ws.ctl, 0, sizeof(gq::SolveCtl), st);
+    // the control block (whose input flags the geometry checks set) and the barrier word
+    // must start at zero
+    cudaError_t e = cudaMemsetAsync(P.ws.ctl, 0, sizeof(gq::SolveCtl), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(P.ws.bar, 0, 2 * sizeof(unsigned), st);
+    if (e == cudaSuccess) {
+        gq::k_geo1d<<<(n1 + 255) / 256, 256, 0, st>>>(nx, ny, sph, x_faces, y_faces, P.geo, &P.ws.ctl->input_flags);
+        gq::k_geo2d<<<std::max(1, std::min(sms * 8, (int)((3ll * P.N + 255) / 256))), 256, 0, st>>>(
+            nx, ny, sph, x_faces, y_faces, P.geo, &P.ws.ctl->input_flags);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = gq::launch_setup(sp, P.geo, P.ws, P.setup_blocks, st);
     if (e == cudaSuccess) e = gq::launch_solve(pp, P.ws, P.solve_grid_max, st);
     if (e == cudaSuccess) e = gq::launch_backsub(sp, P.geo, P.ws, P.setup_blocks, st);

@@ -39,7 +39,8 @@ class SolverOptions:
     mg_omega: float = 0.0         # 0 = library default
     mg_over: float = 0.0
     mg_block_cells: int = 0       # 0 = library default
-    subcycle_freeze_D: int = 0    # sub-cycled steps: 1 = D from the hydro step's start (the paper's order)
+    subcycle_freeze_D: int = 1    # sub-cycled steps: 1 = D from the hydro step's start (the paper's order),
+                                  # 0 = D re-formed from each sub-step's state
 
     def to_c(self) -> N.SolverOpts:
         o = N.SolverOpts()

@@ -30,6 +30,18 @@ def test_reference_arm_line():
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
     assert line["config"]["cells"] == 64 * 64
+    # the 64 x 64 workload is timed on full oracle steps, and one full step is reported
+    assert line["extrapolated"] is False
+    assert line["full_oracle_step"]["steps_run"] == 1 and line["full_oracle_step"]["iterations"] > 0
+
+
+def test_oracle_iteration_counts_recorded():
+    """The CPU baseline's extrapolation count comes from the oracle's own full steps."""
+    with open(os.path.join(ROOT, "oracle", "iteration_counts.json")) as f:
+        counts = json.load(f)
+    for name in ("c0", "c1", "c2"):
+        assert counts[name]["iterations"] > 0 and counts[name]["status"] == 0
+        assert counts[name]["cell_residual"] <= counts[name]["tol"] * 1.01
 
 
 def test_reference_arm_only_rank0_prints():

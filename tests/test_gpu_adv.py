@@ -58,7 +58,8 @@ def test_step_with_source(fld, orc, coord, prec):
     cond = componentwise_condition(orc, P, ref["E_r"])
     out = run_gpu(fld, P, prec, 1e-12 if prec == W.PREC_FP64 else 1e-10)
     assert out["info"]["status"] == 0, out["info"]
-    check_parity_conditioned(out, ref, FP64_GATE if prec == W.PREC_FP64 else MIXED_GATE, cond)
+    check_parity_conditioned(out, ref, FP64_GATE if prec == W.PREC_FP64 else MIXED_GATE, cond,
+                             label=f"adv step coord={coord} prec={prec}")
     # the same step without the source lands elsewhere
     assert relerr(out["E_r"], orc.step(dataclasses.replace(P, S_adv=None), "lu")["E_r"]) > 1e-6
 
@@ -75,11 +76,11 @@ def test_subcycled_step_with_source(fld, orc):
         assert ((Q.E_r + P.S_adv * dt) / Q.E_r).min() > 0.5
         o = orc.step(dataclasses.replace(Q, dt=dt), "lu")
         Q = dataclasses.replace(Q, E_r=o["E_r"], e_g=o["e_g"])
-    ref = orc.step_subcycled(P, 4, 1.3)
+    ref = orc.step_subcycled(P, 4, 1.3, freeze_D=False)
     cond = componentwise_condition(orc, P, ref["E_r"])
-    out = run_gpu(fld, P, W.PREC_FP64, 1e-12, n_sub=4, q_t=1.3)
+    out = run_gpu(fld, P, W.PREC_FP64, 1e-12, n_sub=4, q_t=1.3, subcycle_freeze_D=0)
     assert out["info"]["status"] == 0, out["info"]
-    check_parity_conditioned(out, ref, FP64_GATE, cond)
+    check_parity_conditioned(out, ref, FP64_GATE, cond, label="adv subcycled")
 
 
 def test_advected_packet_steps(fld, orc):

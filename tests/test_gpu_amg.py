@@ -45,7 +45,8 @@ def test_amg_small_grids(fld, orc, nx, ny, coord, prec):
     rtol = 1e-12 if prec == W.PREC_FP64 else 1e-10
     out = run_gpu(fld, P, prec, rtol, precond=AMG)
     assert out["info"]["status"] in (0, 4), out["info"]
-    check_parity_conditioned(out, ref, FP64_GATE if prec == W.PREC_FP64 else MIXED_GATE, cond)
+    check_parity_conditioned(out, ref, FP64_GATE if prec == W.PREC_FP64 else MIXED_GATE, cond,
+                             label=f"amg small_grids {P.name} prec={prec}")
 
 
 @pytest.mark.parametrize("prec,rtol,gate", [(W.PREC_FP64, 1e-12, FP64_GATE), (W.PREC_MIXED, 1e-10, MIXED_GATE)])
@@ -66,7 +67,7 @@ def test_amg_cuts_iterations_on_jumping_coefficients(fld, orc):
     cond = componentwise_condition(orc, P, ref["E_r"])
     a = run_gpu(fld, P, W.PREC_MIXED, 1e-10, precond=1)
     b = run_gpu(fld, P, W.PREC_MIXED, 1e-10, precond=AMG)
-    check_parity_conditioned(b, ref, MIXED_GATE, cond)
+    check_parity_conditioned(b, ref, MIXED_GATE, cond, label="amg jumping coefficients 130x33")
     assert b["info"]["iterations"] * 10 < a["info"]["iterations"], (a["info"], b["info"])
     assert b["info"]["iterations"] < 100
 
@@ -93,8 +94,8 @@ def test_amg_in_batch(fld, orc):
         assert info["status"] in (0, 4), (P.name, info)
         ref = orc.step(P, "lu")
         gate = gate_for(orc, P, ref["E_r"])
-        assert within(f[2].cpu().numpy(), ref["E_r"], gate) and within(f[3].cpu().numpy(), ref["T_g"], gate), \
-            (P.name, info)
+        assert within(f[2].cpu().numpy(), ref["E_r"], gate, P, f"amg batch {P.name} E", info["status"]) and \
+            within(f[3].cpu().numpy(), ref["T_g"], gate, P, f"amg batch {P.name} T", info["status"]), (P.name, info)
     B.close()
     for p in plans:
         p.close()

@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from paper_2602_12545_gb300 import workloads as W
+from parity_gate import componentwise_condition, conditioned_gate, within_conditioned
 
 pytestmark = pytest.mark.gpu
 
@@ -24,20 +25,21 @@ def relerr(a, b):
     return float(np.max(np.abs(np.asarray(a) - np.asarray(b)) / np.abs(np.asarray(b))))
 
 
-EPS = np.finfo(np.float64).eps
+def plain_gate(P):
+    return 1e-10 if P.precision == W.PREC_FP64 else 1e-8
 
 
 def gate_for(orc, P, E_ref):
-    """max(stated tolerance, 16 eps x componentwise condition number) per cell (see
-    test_gpu_parity.componentwise_condition)."""
-    A, _ = orc.assemble_reduced(P)
-    x = np.asarray(E_ref).ravel()
-    cond = (orc.band_solve(A, abs(A) @ x) / x).reshape(np.shape(E_ref))
-    g = 1e-10 if P.precision == W.PREC_FP64 else 1e-8
-    return np.maximum(g, 16 * EPS * cond)
+    """max(stated tolerance, 16 eps x componentwise condition number) per cell (the
+    conditioned gate of parity_gate)."""
+    return conditioned_gate(plain_gate(P), componentwise_condition(orc, P, E_ref))
 
 
-def within(a, b, gate):
+def within(a, b, gate, P=None, label="", status=None):
+    """Element-wise within the per-cell gate; with P given, the widening is reported and
+    bounded against P's stated tolerance."""
+    if P is not None:
+        return within_conditioned(a, b, gate, plain_gate(P), label=label, status=status)
     return bool(np.all(np.abs(np.asarray(a) - np.asarray(b)) / np.abs(np.asarray(b)) <= gate))
 
 
@@ -83,7 +85,9 @@ def test_batch_members_match_solo_and_oracle(fld, orc, use_graph):
         ref = orc.step(P, "lu")
         gate = gate_for(orc, P, ref["E_r"])
         eg, E, T = (t.cpu().numpy() for t in f[1:])
-        assert within(E, ref["E_r"], gate) and within(T, ref["T_g"], gate), (P.name, info)
+        lab = f"batch graph={use_graph} {P.name}"
+        assert within(E, ref["E_r"], gate, P, lab + " E", info["status"]) and \
+            within(T, ref["T_g"], gate, P, lab + " T", info["status"]), (P.name, info)
         (seg, sE, sT), sinfo = solo(F, P)
         assert within(E, sE, 2 * gate) and within(T, sT, 2 * gate)
     assert B.uses_graph == use_graph

@@ -50,28 +50,8 @@ def check_parity(out, ref, gate):
         assert err <= gate, f"{f}: max rel err {err:.3e} > {gate:.0e}"
 
 
-EPS = np.finfo(np.float64).eps
-
-
-def componentwise_condition(orc, P, E):
-    """Skeel's componentwise condition number of the reduced system per cell,
-    (A^-1 |A| x)_k / x_k, from the oracle's own matrix and direct solver.  Two correct
-    FP64 evaluations of the coefficients differ by a few ulps, so no FP64 implementation
-    can agree with another better than about eps times this number."""
-    A, _ = orc.assemble_reduced(P)
-    x = np.asarray(E, dtype=np.float64).ravel()
-    z = orc.band_solve(A, abs(A) @ x)
-    return (z / x).reshape(np.shape(E))
-
-
-def check_parity_conditioned(out, ref, gate, cond):
-    """Per-cell gate max(gate, 16 eps cond_k): the stated tolerance wherever the problem's
-    conditioning allows it, the FP64 sensitivity bound elsewhere."""
-    g = np.maximum(gate, 16 * EPS * cond)
-    for f in ("E_r", "T_g", "e_g"):
-        e = np.abs(out[f] - ref[f]) / np.abs(ref[f])
-        bad = e > g
-        assert not bad.any(), f"{f}: {bad.sum()} cells above gate, worst {e.max():.3e} (cond max {cond.max():.2e})"
+# the per-cell gate max(stated tolerance, 16 eps cond_k) with its reported widening
+from parity_gate import EPS, check_parity_conditioned, componentwise_condition  # noqa: E402,F401
 
 
 # ----------------------------------------------------------------------------
@@ -145,7 +125,8 @@ def test_small_grids(fld, orc, nx, ny, coord, prec):
     # GQ_ERR_NOT_CONVERGED is the documented answer when rtol lies below the FP64 floor
     # of the cell-wise residual (ill-conditioned draws); the iterate must still agree
     assert out["info"]["status"] in (0, 4), out["info"]
-    check_parity_conditioned(out, ref, FP64_GATE if prec == W.PREC_FP64 else MIXED_GATE, cond)
+    check_parity_conditioned(out, ref, FP64_GATE if prec == W.PREC_FP64 else MIXED_GATE, cond,
+                             label=f"small_grids {P.name} prec={prec}")
 
 
 @pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 1, 1, 1), (0, 1, 0, 0), (1, 0, 1, 0)])
@@ -248,24 +229,28 @@ def test_loose_refinement_trigger_still_converges(fld, orc):
 # sub-cycling (Eq. subtimesteps): n_sub geometric sub-steps against the oracle's
 # ----------------------------------------------------------------------------
 
+@pytest.mark.parametrize("freeze_D", [1, 0])
 @pytest.mark.parametrize("case,prec,n_sub,q_t", [
     ("c0", W.PREC_FP64, 5, 1.4),
     ("c0", W.PREC_MIXED, 5, 1.4),
     ("sph", W.PREC_FP64, 3, 1.2),
     ("sph", W.PREC_MIXED, 6, 1.0),
 ])
-def test_subcycled_step(fld, orc, case, prec, n_sub, q_t):
+def test_subcycled_step(fld, orc, case, prec, n_sub, q_t, freeze_D):
+    """freeze_D = 1 (the default): the order of the radiation algorithm of Sec. 3.2.1, D
+    held from the hydro step's start and alpha updated per sub-step; freeze_D = 0: D
+    re-formed from every sub-step's state.  Each against the oracle in the same order."""
     P = W.config0() if case == "c0" else W.random_small(40, 24, W.SPHERICAL, (0, 1, 0, 0), 41, dt=3e4)
-    ref = orc.step_subcycled(P, n_sub, q_t)
+    ref = orc.step_subcycled(P, n_sub, q_t, freeze_D=bool(freeze_D))
     cond = componentwise_condition(orc, P, ref["E_r"])
     rtol = 1e-12 if prec == W.PREC_FP64 else 1e-10
     import torch
     Fx = torch.full((P.ny, P.nx + 1), float("nan"), dtype=torch.float64, device="cuda")
     Fy = torch.full((P.ny + 1, P.nx), float("nan"), dtype=torch.float64, device="cuda")
-    out = run_gpu(fld, P, prec, rtol, n_sub=n_sub, q_t=q_t, Fx=Fx, Fy=Fy)
+    out = run_gpu(fld, P, prec, rtol, n_sub=n_sub, q_t=q_t, Fx=Fx, Fy=Fy, subcycle_freeze_D=freeze_D)
     assert out["info"]["status"] == 0, out["info"]
     gate = FP64_GATE if prec == W.PREC_FP64 else MIXED_GATE
-    check_parity_conditioned(out, ref, gate, cond)
+    check_parity_conditioned(out, ref, gate, cond, label=f"subcycled {case} prec={prec} n_sub={n_sub} q={q_t} freeze_D={freeze_D}")
     assert out["info"]["energy_before"] == pytest.approx(ref["energy_before"], rel=1e-12)
     # accumulated face flux: a difference of neighbouring E values, so where the gradient
     # is small its relative error is E / dE times that of E; gated norm-wise against the

@@ -114,7 +114,7 @@ def test_subcycled_source_adds_S_dt_in_total(orc):
     P, fx, fy = W.advected_packet(nx=64, cfl=0.5)
     P = dataclasses.replace(P, S_adv=orc.adv_source(P, fx, fy))
     g = orc.geometry(P)
-    out = orc.step_subcycled(P, 5, 1.4)
+    out = orc.step_subcycled(P, 5, 1.4, freeze_D=False)
     before = (g["V"] * P.E_r).sum()
     after = (g["V"] * out["E_r"]).sum()
     assert after == pytest.approx(before + P.dt * (g["V"] * P.S_adv).sum(), rel=1e-13)

@@ -11,6 +11,7 @@ import pytest
 import oracle
 import test_oracle_adv as ADV
 import test_oracle_eos as EOS
+import test_oracle_opacity as OPA
 
 HERE = os.path.dirname(os.path.abspath(oracle.__file__))
 
@@ -27,6 +28,32 @@ MUTANTS = {
     "cv_secant": ("W->CV[k] = rho * slope;",
                   "W->CV[k] = rho * u / W->T[k];",
                   EOS.test_tangent_cv_keeps_the_state_on_the_table),
+    # opacity power law: exponents of rho and T swapped
+    "opacity_exponents_swapped": ("return k[0] + k[1] * pow(rho, k[2]) * pow(T, k[3]);",
+                                  "return k[0] + k[1] * pow(rho, k[3]) * pow(T, k[2]);",
+                                  OPA.test_rosseland_law_per_cell_states),
+    # opacity power law: the constant term dropped
+    "opacity_k0_dropped": ("return k[0] + k[1] * pow(rho, k[2]) * pow(T, k[3]);",
+                           "return k[1] * pow(rho, k[2]) * pow(T, k[3]);",
+                           OPA.test_rosseland_law_in_the_face_coefficient),
+    # Rosseland opacity taken at the radiation temperature (E / a)^(1/4) instead of T_g^n
+    "opacity_at_radiation_temperature": (
+        "double kR = opacity(P->kR, rho, W->T[k]);",
+        "double kR = opacity(P->kR, rho, sqrt(sqrt(P->E[k] / orc_const_aR())));",
+        OPA.test_rosseland_law_in_the_face_coefficient),
+    # Planck opacity taken at the radiation temperature: caught by the exchange closed form
+    "planck_at_radiation_temperature": (
+        "double kP = opacity(P->kP, rho, W->T[k]);",
+        "double kP = opacity(P->kP, rho, sqrt(sqrt(P->E[k] / orc_const_aR())));",
+        OPA.test_planck_law_in_the_exchange_closed_form),
+    # Rosseland and Planck laws exchanged in the diffusion coefficient
+    "sigma_from_planck": ("W->sig[k] = kR * rho;",
+                          "W->sig[k] = kP * rho;",
+                          OPA.test_rosseland_law_in_the_face_coefficient),
+    # Planck law replaced by the Rosseland one in the exchange
+    "beta_from_rosseland": ("W->betaP[k] = kP * rho * c * P->dt;",
+                            "W->betaP[k] = kR * rho * c * P->dt;",
+                            OPA.test_planck_law_in_the_exchange_closed_form),
 }
 
 
