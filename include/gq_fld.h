@@ -459,6 +459,55 @@ size_t gq_server_used_bytes(gq_server *server);
 /* Destroy the server and everything it holds (NULL is ignored). */
 void gq_server_destroy(gq_server *server);
 
+/* ---------------------------------------------------------------------------------------
+ * Multilevel (statically refined) grids, Sec. 3.2.2 (Eq. linearsys1_amr and the figure of
+ * the interpolation at a level jump): one implicit FLD step over a two-level Cartesian grid
+ * whose base cells in one rectangle are replaced by 2 x 2 fine cells.  All composite cells
+ * enter one linear system: across a level jump, a coarse cell couples directly to each of
+ * the two fine cells beside its side, so it has five neighbours, and each such face is a
+ * fine face (half a coarse side) whose weight dt A D / d both cells share.  Face values of
+ * E and kappa_R rho are linear in the normal coordinate between the two centres (3/4 of a
+ * coarse width apart across the jump), R uses their normal difference over that distance,
+ * and the coarse centre's tangential offset is not used.  Everything else is the
+ * single-level step (C_V, opacities at T_g^n, the limiter, Milne and reflecting sides, T
+ * eliminated from the psi row, the cell-wise stop rule).
+ * --------------------------------------------------------------------------------------- */
+
+/* Two-level grid: nx x ny base cells of widths dx, dy (cm) from the origin; base cells
+ * i0 <= i < i1, j0 <= j < j1 are refined (i0 == i1 or j0 == j1: no refinement; otherwise
+ * 0 <= i0 < i1 <= nx, 0 <= j0 < j1 <= ny).  Composite cell order, for every field array:
+ * the base cells outside the rectangle in row-major order, then the 2 (i1 - i0) x
+ * 2 (j1 - j0) fine cells in row-major order (x fastest). */
+typedef struct {
+    int nx, ny;
+    double dx, dy;
+    int i0, i1, j0, j1;
+} gq_smr_grid;
+
+typedef struct gq_smr_plan gq_smr_plan;
+
+/* Build a plan: the composite cell list, its faces (interior, with the neighbour pair,
+ * A / d and the interpolation weight; boundary, with A / h) and the workspace of one step,
+ * computed on the host and uploaded.  Errors: GQ_ERR_INVALID_ARG (sizes, widths not
+ * positive and finite, a rectangle outside the grid), GQ_ERR_OOM, GQ_ERR_CUDA. */
+gq_status gq_smr_setup(const gq_smr_grid *grid, gq_smr_plan **out);
+
+/* Composite cells of a plan (0 for NULL). */
+int gq_smr_cells(const gq_smr_plan *plan);
+
+/* One implicit step on the composite grid.  rho, e_g, E_r, T_g_out: DEVICE arrays of
+ * gq_smr_cells(plan) doubles in composite order, with the meaning and ownership of
+ * gq_fld_step's.  The composite system is solved by Jacobi-preconditioned conjugate
+ * gradients (opts->precond and the multigrid options are not used), FP64 or FP32 inner
+ * iterations inside FP64 iterative refinement (opts->prec), to the cell-wise relative
+ * residual opts->rtol; eos must be the ideal gas (table_n = 0).  Errors as gq_fld_step. */
+gq_status gq_smr_step(gq_smr_plan *plan, const double *rho, double *e_g, double *E_r, double *T_g_out,
+                      const gq_opacity_law *opacity, const gq_eos *eos, double dt, const gq_bc *bc,
+                      const gq_solver_opts *opts, void *stream, gq_step_info *info);
+
+/* Release a plan (NULL is ignored). */
+void gq_smr_destroy(gq_smr_plan *plan);
+
 /* Default solver options: FP64, LP limiter, rtol 1e-10, max_iter 200000, inner_rtol 0.1,
  * max_refine 200, default spin limit, keep the search direction, algebraic multigrid
  * preconditioning (omega 0.8; coarse factor 1.5 for the aggregation cycle), sub-cycled

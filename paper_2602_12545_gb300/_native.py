@@ -83,6 +83,11 @@ class PrecondInfo(ctypes.Structure):
                 "outside_cycle_ms": sum(self.cycle_ms[20:24])}
 
 
+class SmrGrid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+                ("i0", ctypes.c_int), ("i1", ctypes.c_int), ("j0", ctypes.c_int), ("j1", ctypes.c_int)]
+
+
 class BatchItem(ctypes.Structure):
     _fields_ = [("rho", ctypes.c_void_p), ("e_g", ctypes.c_void_p), ("E_r", ctypes.c_void_p),
                 ("T_g_out", ctypes.c_void_p), ("opacity", OpacityLaw), ("eos", Eos), ("dt", ctypes.c_double),
@@ -148,6 +153,13 @@ SIGNATURES = {
                                            ctypes.POINTER(Bc), ctypes.POINTER(SolverOpts), ctypes.c_void_p,
                                            ctypes.POINTER(StepInfo)]),
     "gq_fld_step_noalloc_max_bytes": (ctypes.c_size_t, []),
+    "gq_smr_setup": (ctypes.c_int, [ctypes.POINTER(SmrGrid), ctypes.POINTER(ctypes.c_void_p)]),
+    "gq_smr_cells": (ctypes.c_int, [ctypes.c_void_p]),
+    "gq_smr_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.POINTER(OpacityLaw), ctypes.POINTER(Eos),
+                                   ctypes.c_double, ctypes.POINTER(Bc), ctypes.POINTER(SolverOpts),
+                                   ctypes.c_void_p, ctypes.POINTER(StepInfo)]),
+    "gq_smr_destroy": (None, [ctypes.c_void_p]),
     "gq_solver_opts_default": (None, [ctypes.POINTER(SolverOpts)]),
     "gq_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "gq_version": (ctypes.c_char_p, []),

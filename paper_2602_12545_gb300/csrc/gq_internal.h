@@ -228,6 +228,11 @@ cudaError_t launch_setup(const StepParams& sp, const DeviceGeometry& g, const Wo
 cudaError_t launch_solve(const SolveParams& p, const Workspace& w, int grid, cudaStream_t st);
 cudaError_t launch_backsub(const StepParams& sp, const DeviceGeometry& g, const Workspace& w,
                            int setup_blocks, cudaStream_t st);
+// the per-cell pass of the set-up alone (C_V, T^n, opacities, the mass term and right-hand
+// side of the reduced system, input checks, energy before the step): the multilevel step
+// forms its faces and operator itself
+cudaError_t launch_cells(const StepParams& sp, const DeviceGeometry& g, const Workspace& w, int setup_blocks,
+                         cudaStream_t st);
 cudaError_t launch_adv_source(int nx, int ny, const DeviceGeometry& g, const double* rho, const double* E,
                               const double* fx, const double* fy, double* S, int nblk, cudaStream_t st);
 cudaError_t launch_face_flux(const StepParams& sp, const DeviceGeometry& g, const Workspace& w, double weight,

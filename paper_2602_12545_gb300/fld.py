@@ -194,6 +194,61 @@ class FLDPlan:
         return out
 
 
+class SMRPlan:
+    """gq_smr_setup / gq_smr_step / gq_smr_destroy: one implicit step on a two-level
+    Cartesian grid (nx x ny base cells of widths dx, dy; base cells [i0, i1) x [j0, j1)
+    refined 2 x 2).  Fields are float64 CUDA tensors of `cells` values in composite order
+    (base cells outside the rectangle row-major, then the fine cells row-major)."""
+
+    def __init__(self, nx: int, ny: int, dx: float, dy: float, i0: int = 0, i1: int = 0, j0: int = 0, j1: int = 0):
+        g = N.SmrGrid(int(nx), int(ny), float(dx), float(dy), int(i0), int(i1), int(j0), int(j1))
+        h = ctypes.c_void_p()
+        self.device = torch.cuda.current_device()
+        rc = N.load().gq_smr_setup(ctypes.byref(g), ctypes.byref(h))
+        if rc != N.GQ_OK:
+            raise N.GQError(rc, "gq_smr_setup")
+        self._h = h
+        self.cells = int(N.load().gq_smr_cells(h))
+
+    def step(self, rho: torch.Tensor, e_g: torch.Tensor, E_r: torch.Tensor, T_out: Optional[torch.Tensor] = None,
+             *, opacity_R: Sequence[float], opacity_P: Sequence[float], gamma: float, mu: float, dt: float,
+             bc: Sequence[int], opts: SolverOptions, stream: Optional[torch.cuda.Stream] = None,
+             check: bool = True) -> dict:
+        for t, n in ((rho, "rho"), (e_g, "e_g"), (E_r, "E_r"), (T_out, "T_out")):
+            if t is None and n == "T_out":
+                continue
+            if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous() or t.numel() != self.cells:
+                raise ValueError(f"{n} must be a contiguous float64 CUDA tensor of {self.cells} elements")
+        op = N.OpacityLaw(*[float(v) for v in tuple(opacity_R) + tuple(opacity_P)])
+        eos = N.Eos(float(gamma), float(mu))
+        b = N.Bc()
+        for i in range(4):
+            b.side[i] = int(bc[i])
+        o = opts.to_c()
+        info = N.StepInfo()
+        st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        rc = N.load().gq_smr_step(self._h, rho.data_ptr(), e_g.data_ptr(), E_r.data_ptr(),
+                                  T_out.data_ptr() if T_out is not None else None, ctypes.byref(op),
+                                  ctypes.byref(eos), float(dt), ctypes.byref(b), ctypes.byref(o),
+                                  ctypes.c_void_p(st), ctypes.byref(info))
+        out = info.as_dict()
+        out["status"] = rc
+        if check and rc != N.GQ_OK:
+            raise N.GQError(rc, "gq_smr_step")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            N.load().gq_smr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def device_fields(p: FLDProblem, device="cuda"):
     """Copy a problem's fields to the device (float64): rho, e_g, E_r, T_out."""
     rho = torch.from_numpy(np.ascontiguousarray(p.rho)).to(device)

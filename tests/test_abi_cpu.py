@@ -91,3 +91,16 @@ def _fresh_load(N, tmp_path):
         N.load(str(tmp_path / "missing.so"))
     finally:
         N._lib = saved
+
+
+def test_smr_setup_rejects_bad_grids_on_the_host(lib_path):
+    """gq_smr_setup validates the grid before touching the device: no GPU needed."""
+    from paper_2602_12545_gb300 import _native as N
+    L = N.load()
+    for nx, ny, dx, dy, i0, i1, j0, j1 in ((0, 4, 1.0, 1.0, 0, 0, 0, 0), (4, 4, -1.0, 1.0, 0, 0, 0, 0),
+                                           (4, 4, 1.0, float("nan"), 0, 0, 0, 0), (4, 4, 1.0, 1.0, 2, 5, 0, 2),
+                                           (4, 4, 1.0, 1.0, 3, 1, 0, 2), (4, 4, 1.0, 1.0, 0, 2, -1, 2)):
+        g = N.SmrGrid(nx, ny, dx, dy, i0, i1, j0, j1)
+        h = ctypes.c_void_p()
+        assert L.gq_smr_setup(ctypes.byref(g), ctypes.byref(h)) == N.GQ_ERR_INVALID_ARG
+        assert not h.value

@@ -17,7 +17,7 @@ PAIRS = {
     "gq_grid_desc": N.GridDesc, "gq_opacity_law": N.OpacityLaw, "gq_eos": N.Eos, "gq_bc": N.Bc,
     "gq_solver_opts": N.SolverOpts, "gq_step_info": N.StepInfo, "gq_precond_info": N.PrecondInfo,
     "gq_batch_item": N.BatchItem, "gq_batch_opts": N.BatchOpts, "gq_server_opts": N.ServerOpts,
-    "gq_request": N.Request, "gq_request_info": N.RequestInfo,
+    "gq_request": N.Request, "gq_request_info": N.RequestInfo, "gq_smr_grid": N.SmrGrid,
 }
 
 
