@@ -133,7 +133,12 @@ typedef struct { int side[4]; } gq_bc;
  *               step's start state E^n, T^n, with its own dt: the order of the radiation
  *               algorithm of Sec. 3.2.1, which updates alpha and keeps D between sub-steps.
  *               0: each sub-step re-forms them from the state it starts from.
- *               Other values: GQ_ERR_INVALID_ARG. */
+ *               Other values: GQ_ERR_INVALID_ARG.
+ *   untiled     0 (default): the mixed path with GQ_PRECOND_MG runs the tiled solve
+ *               kernel (each multigrid level the whole grid works on in two fused passes
+ *               over shared-memory tiles) where every such level has a width divisible by
+ *               8 and an even height; 1: always the untiled kernel.  Both compute the same
+ *               cycle; other values: GQ_ERR_INVALID_ARG. */
 typedef struct {
     int prec;
     int limiter;
@@ -149,7 +154,7 @@ typedef struct {
     double mg_omega;
     double mg_over;
     int subcycle_freeze_D;
-    int reserved;
+    int untiled;
 } gq_solver_opts;
 
 /* Result of one step (host struct). */
@@ -168,7 +173,7 @@ typedef struct {
     float t_precond_ms;         /* device clock: build of the preconditioner inside the solve */
     float t_iter_us;            /* device clock: solve time after that build per Krylov iteration */
     int precond_levels;         /* levels of the multigrid hierarchy (1 for Jacobi) */
-    int reserved;
+    int solve_kernel;           /* the solve kernel that ran: 0 untiled, 1 tiled (see opts.untiled) */
 } gq_step_info;
 
 typedef struct gq_fld_plan gq_fld_plan;

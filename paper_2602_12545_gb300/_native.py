@@ -50,7 +50,7 @@ class SolverOpts(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("inner_rtol", ctypes.c_double), ("max_refine", ctypes.c_int),
                 ("spin_limit", ctypes.c_int64), ("restart", ctypes.c_int), ("timing", ctypes.c_int),
                 ("precond", ctypes.c_int), ("mg_block_cells", ctypes.c_int), ("mg_omega", ctypes.c_double),
-                ("mg_over", ctypes.c_double), ("subcycle_freeze_D", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("mg_over", ctypes.c_double), ("subcycle_freeze_D", ctypes.c_int), ("untiled", ctypes.c_int)]
 
 
 class StepInfo(ctypes.Structure):
@@ -59,7 +59,7 @@ class StepInfo(ctypes.Structure):
                 ("energy_after", ctypes.c_double), ("status", ctypes.c_int), ("solve_blocks", ctypes.c_int),
                 ("t_setup_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double), ("t_finish_ms", ctypes.c_double),
                 ("t_precond_ms", ctypes.c_float), ("t_iter_us", ctypes.c_float), ("precond_levels", ctypes.c_int),
-                ("reserved", ctypes.c_int)]
+                ("solve_kernel", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}

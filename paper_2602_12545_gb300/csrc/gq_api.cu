@@ -282,6 +282,7 @@ gq_status make_step_params(const gq_fld_plan* P, const double* rho, double* e_g,
     if (!(omega > 0.0 && omega <= 1.0) || !(over > 0.0 && over < 2.0)) return GQ_ERR_INVALID_ARG;
     if (opts.mg_block_cells < 0) return GQ_ERR_INVALID_ARG;
     if (opts.subcycle_freeze_D != 0 && opts.subcycle_freeze_D != 1) return GQ_ERR_INVALID_ARG;
+    if (opts.untiled != 0 && opts.untiled != 1) return GQ_ERR_INVALID_ARG;
 
     StepParams sp{};
     sp.nx = P->nx;
@@ -325,6 +326,7 @@ gq_status make_step_params(const gq_fld_plan* P, const double* rho, double* e_g,
     pp.mg_omega = (float)omega;
     pp.mg_over = (float)over;
     pp.block_cells = opts.mg_block_cells > 0 ? opts.mg_block_cells : gq::kBlockLevelMax;
+    pp.tiled = opts.untiled ? 0 : 1;
     *sp_out = sp;
     *pp_out = pp;
     if (timing) *timing = opts.timing;
@@ -564,7 +566,8 @@ gq_status gq_fld_step(gq_fld_plan* P, const double* rho, double* e_g, double* E_
     if (e == cudaSuccess && timing) e = cudaEventRecord(P->ev[0], st);
     if (e == cudaSuccess) e = gq::launch_setup(sp, P->geo, P->ws, P->setup_blocks, st);
     if (e == cudaSuccess && timing) e = cudaEventRecord(P->ev[1], st);
-    if (e == cudaSuccess) e = gq::launch_solve(pp, P->ws, P->solve_grid_max, st);
+    int kernel = 0;
+    if (e == cudaSuccess) e = gq::launch_solve(pp, P->ws, P->solve_grid_max, st, &kernel);
     if (e == cudaSuccess && timing) e = cudaEventRecord(P->ev[2], st);
     if (e == cudaSuccess) e = gq::launch_backsub(sp, P->geo, P->ws, P->setup_blocks, st);
     if (e == cudaSuccess && timing) e = cudaEventRecord(P->ev[3], st);
@@ -581,6 +584,7 @@ gq_status gq_fld_step(gq_fld_plan* P, const double* rho, double* e_g, double* E_
     if (info) {
         gq::fill_info(c, status, info);
         info->solve_blocks = P->solve_grid_max;
+        info->solve_kernel = kernel;
         if (timing) {
             float t0 = 0.f, t1 = 0.f, t2 = 0.f;
             cudaEventElapsedTime(&t0, P->ev[0], P->ev[1]);
@@ -674,6 +678,7 @@ gq_status gq_fld_step_subcycled(gq_fld_plan* P, const double* rho, double* e_g, 
         acc.t_finish_ms += si.t_finish_ms;
         acc.t_precond_ms += si.t_precond_ms;
         acc.precond_levels = si.precond_levels;
+        acc.solve_kernel = si.solve_kernel;
         if (s == GQ_ERR_NOT_CONVERGED) {
             result = s;
         } else if (s != GQ_OK) {

@@ -183,6 +183,7 @@ struct SolveParams {
     float mg_omega;      // Jacobi smoothing weight of the V-cycle
     float mg_over;       // coarse-correction over-relaxation
     int block_cells;     // multigrid levels up to this size run in one block
+    int tiled;           // 1: the tiled solve kernel where the problem allows it
 };
 
 // status of a problem of a batch that no team has solved yet
@@ -225,7 +226,8 @@ struct BatchArgs {
 // launchers (stream-ordered)
 cudaError_t launch_setup(const StepParams& sp, const DeviceGeometry& g, const Workspace& w,
                          int setup_blocks, cudaStream_t st);
-cudaError_t launch_solve(const SolveParams& p, const Workspace& w, int grid, cudaStream_t st);
+// *kernel (may be null) receives the kernel launched: 0 k_pcg, 1 k_pcg_tiled
+cudaError_t launch_solve(const SolveParams& p, const Workspace& w, int grid, cudaStream_t st, int* kernel = nullptr);
 cudaError_t launch_backsub(const StepParams& sp, const DeviceGeometry& g, const Workspace& w,
                            int setup_blocks, cudaStream_t st);
 // the per-cell pass of the set-up alone (C_V, T^n, opacities, the mass term and right-hand
@@ -238,6 +240,10 @@ cudaError_t launch_adv_source(int nx, int ny, const DeviceGeometry& g, const dou
 cudaError_t launch_face_flux(const StepParams& sp, const DeviceGeometry& g, const Workspace& w, double weight,
                              bool accumulate, double* Fx, double* Fy, int nblk, cudaStream_t st);
 int solve_max_blocks_per_sm();
+// the tiled solve (gq_pcg_tiled.cu): its kernel, dynamic shared memory and eligibility
+const void* solve_kernel_tiled();
+size_t tiled_smem_bytes();
+bool tiled_eligible(const SolveParams& p, const Workspace& w);
 int batch_solve_max_blocks_per_sm();
 cudaError_t launch_batch_setup(const BatchArgs& a, int total_setup_blocks, cudaStream_t st);
 cudaError_t launch_batch_solve(const BatchArgs& a, int grid, cudaStream_t st);

@@ -1,0 +1,738 @@
+// Tiled single-problem solve: mixed-precision conjugate gradients preconditioned by the
+// aggregation-multigrid V-cycle (the Krylov step of Sec. 3.2.1 with the preconditioner of
+// gq_mg.cuh), restructured so that every multigrid level the whole grid of blocks works
+// on costs two passes and two grid barriers per cycle instead of four.
+//
+// A pass walks the level in tiles of kTX x kTY cells.  Each block stages a tile's inputs
+// with a halo (kHX = 4 cells in x, one 16-byte chunk; kHY = 2 rows in y) into shared
+// memory by cp.async (zero-filled outside the grid, double-buffered so that the next
+// tile's loads overlap this tile's arithmetic), and computes what needs neighbours from
+// the staged copy, redundantly on the halo:
+//   down pass (level l):  x_a = omega (2 r - omega A r) on the tile and a one-cell ring,
+//                         then the residual r - A x_a on the tile, restricted to level
+//                         l + 1 (2 x 2 aggregates, transfer weights t);
+//   up pass (level l):    x~ = x_a + over t x_{l+1}(parent) on the tile and two rings,
+//                         x_b = x~ + omega (r - A x~) on the tile and one ring,
+//                         out = x_b + omega (r - A x_b) on the tile;
+//   level 0 down pass:    fused with the Krylov update r' = r - alpha q, d += alpha p
+//                         (r' formed on the staged region from r and q), with r'.r';
+//   level 0 up pass:      out = z, with the partial sums r.z and r.z_old.
+// These are the same operations, in the same order, as the cycle of gq_mg.cuh (two
+// weighted-Jacobi sweeps from zero fused into one, residual and restriction,
+// prolongation with the factor `over` and one sweep, a final sweep); only the pass
+// boundaries move.  The levels of at most block_cells cells run in the team's first
+// block as before, and the direction pass (p = z + beta p_old, q = A p, p.q), the FP64
+// refinement and the stop tests are those of k_pcg.
+//
+// Used for the mixed path with the aggregation preconditioner when every level the
+// whole grid works on has a width divisible by 8 and an even height (16-byte staging
+// chunks on the level and on its parent); other problems use k_pcg.
+#include "gq_pcg.cuh"
+
+namespace gq {
+namespace {
+
+constexpr int kTX = 64, kTY = 16;      // tile of a level (cells)
+constexpr int kHX = 4, kHY = 2;        // staged halo: x one 16-byte chunk, y two rows
+constexpr int kRW = kTX + 2 * kHX;     // staged region width (72)
+constexpr int kRH = kTY + 2 * kHY;     // staged region height (20)
+constexpr int kNR = kRW * kRH;
+constexpr int kCW = kTX / 2 + 8;       // staged coarse region (40 x 12)
+constexpr int kCH = kTY / 2 + 4;
+constexpr int kNC = kCW * kCH;
+constexpr int kStaged = 5;             // staged arrays per tile
+
+struct TileSmem {
+    float in[2][kStaged][kNR];         // staged inputs, two buffers
+    float co[2][kNC];                  // staged coarse values (up passes)
+    float c1[kNR];                     // computed: x_a (down) or x~ (up)
+    float c2[kNR];                     // computed: x_b (up)
+};
+
+__device__ __forceinline__ void cp16(float* dst, const float* src, bool ok) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// stage the region of g (nx x ny, nx % 4 == 0) with origin (X0, Y0), X0 % 4 == 0, size
+// RW x RH (RW % 4 == 0) into dst; chunks outside the grid are zero-filled
+template <int RW, int RH>
+__device__ __forceinline__ void stage(float* dst, const float* g, int nx, int ny, int X0, int Y0) {
+    constexpr int CPR = RW / 4;
+    for (int c = threadIdx.x; c < CPR * RH; c += blockDim.x) {
+        const int row = c / CPR, col = c - row * CPR;
+        const int gx = X0 + 4 * col, gy = Y0 + row;
+        const bool ok = gy >= 0 && gy < ny && gx >= 0 && gx < nx;
+        cp16(dst + row * RW + 4 * col, ok ? g + (size_t)gy * nx + gx : g, ok);
+    }
+}
+
+// (A v) at region index i: unit diagonal, couplings staged like v
+__device__ __forceinline__ float st5(const float* v, const float* cw, const float* cs, int i) {
+    return v[i] - cw[i] * v[i - 1] - cw[i + 1] * v[i + 1] - cs[i] * v[i - kRW] - cs[i + kRW] * v[i + kRW];
+}
+
+struct TLevel {
+    int nx, ny;                // cells (nx % 8 == 0, ny even)
+    const float* cW;
+    const float* cS;
+    const float* t;            // transfer weight to the parent
+    const float* r;            // right-hand side (level 0: the Krylov residual)
+    float* xa;                 // pre-smoothed values (kept for the up pass)
+    float* out;                // result of the level (level 0: z)
+    float* rc;                 // the parent's right-hand side (restriction target)
+    const float* xc;           // the parent's result (prolongation source)
+    int cnx, cny;              // parent dimensions
+};
+
+__device__ __forceinline__ int ntiles(const TLevel& L) { return ((L.nx + kTX - 1) / kTX) * ((L.ny + kTY - 1) / kTY); }
+
+__device__ __forceinline__ void tile_origin(const TLevel& L, int t, int& x0, int& y0) {
+    const int tx = (L.nx + kTX - 1) / kTX;
+    const int ty = t / tx;
+    x0 = (t - ty * tx) * kTX;
+    y0 = ty * kTY;
+}
+
+// Kernel-wide arguments of the fused level-0 down pass: the Krylov update.
+struct UpdateArgs {
+    bool on;                   // false: plain down pass on r
+    float alpha;
+    const float* q;            // q = A p
+    const float* p;            // the direction
+    float* d;                  // correction (updated in place)
+    float* rnew;               // r' (written for the tile)
+};
+
+// Down pass of one level over all of its tiles this block owns (tiles b, b + G, ...).
+// Staged: 0 r (or r_old), 1 q (update only), 2 cW, 3 cS, 4 t.
+__device__ void down_pass(const TLevel& L, float om, const UpdateArgs& U, TileSmem& S, int b, int G, double* rr) {
+    const int nt = ntiles(L);
+    auto issue = [&](int t, int buf) {
+        int x0, y0;
+        tile_origin(L, t, x0, y0);
+        const int X0 = x0 - kHX, Y0 = y0 - kHY;
+        stage<kRW, kRH>(S.in[buf][0], L.r, L.nx, L.ny, X0, Y0);
+        if (U.on) stage<kRW, kRH>(S.in[buf][1], U.q, L.nx, L.ny, X0, Y0);
+        stage<kRW, kRH>(S.in[buf][2], L.cW, L.nx, L.ny, X0, Y0);
+        stage<kRW, kRH>(S.in[buf][3], L.cS, L.nx, L.ny, X0, Y0);
+        stage<kRW, kRH>(S.in[buf][4], L.t, L.nx, L.ny, X0, Y0);
+        cp_commit();
+    };
+    if (b < nt) issue(b, 0);
+    int i = 0;
+    for (int t = b; t < nt; t += G, i++) {
+        const int buf = i & 1;
+        if (t + G < nt) {
+            issue(t + G, buf ^ 1);
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
+        }
+        __syncthreads();
+        int x0, y0;
+        tile_origin(L, t, x0, y0);
+        float* R = S.in[buf][0];
+        const float* Q = S.in[buf][1];
+        const float* CW = S.in[buf][2];
+        const float* CS = S.in[buf][3];
+        const float* T = S.in[buf][4];
+        float* XA = S.c1;
+        if (U.on) {
+            // r' = r - alpha q on the whole staged region (zeros stay zeros)
+            for (int e = threadIdx.x; e < kNR; e += blockDim.x) R[e] = R[e] - U.alpha * Q[e];
+            __syncthreads();
+        }
+        // x_a on the tile and a one-cell ring
+        constexpr int AW = kTX + 2, AH = kTY + 2;
+        for (int e = threadIdx.x; e < AW * AH; e += blockDim.x) {
+            const int ly = e / AW, lx = e - ly * AW;
+            const int ix = (kHY - 1 + ly) * kRW + (kHX - 1 + lx);
+            XA[ix] = om * (2.f * R[ix] - om * st5(R, CW, CS, ix));
+        }
+        __syncthreads();
+        // residual on the tile, restricted to the parent (one thread per 2 x 2 aggregate)
+        constexpr int CX = kTX / 2, CY = kTY / 2;
+        for (int e = threadIdx.x; e < CX * CY; e += blockDim.x) {
+            const int cj = e / CX, ci = e - cj * CX;
+            float acc = 0.f;
+#pragma unroll
+            for (int dy = 0; dy < 2; dy++)
+#pragma unroll
+                for (int dx = 0; dx < 2; dx++) {
+                    const int ix = (kHY + 2 * cj + dy) * kRW + (kHX + 2 * ci + dx);
+                    acc += T[ix] * (R[ix] - st5(XA, CW, CS, ix));
+                }
+            const int gi = x0 / 2 + ci, gj = y0 / 2 + cj;
+            if (gi < L.cnx && gj < L.cny) L.rc[(size_t)gj * L.cnx + gi] = acc;
+        }
+        // the tile's x_a (and, fused with the update, r', d and r'.r')
+        constexpr int Q4 = kTX / 4;
+        for (int e = threadIdx.x; e < Q4 * kTY; e += blockDim.x) {
+            const int ly = e / Q4, q4 = e - ly * Q4;
+            const int gx = x0 + 4 * q4, gy = y0 + ly;
+            if (gx >= L.nx || gy >= L.ny) continue;
+            const int ix = (kHY + ly) * kRW + (kHX + 4 * q4);
+            const size_t g = (size_t)gy * L.nx + gx;
+            *reinterpret_cast<float4*>(L.xa + g) = make_float4(XA[ix], XA[ix + 1], XA[ix + 2], XA[ix + 3]);
+            if (U.on) {
+                const float4 rn = make_float4(R[ix], R[ix + 1], R[ix + 2], R[ix + 3]);
+                *reinterpret_cast<float4*>(U.rnew + g) = rn;
+                const float4 pk = __ldcg(reinterpret_cast<const float4*>(U.p + g));
+                float4 dk = __ldcg(reinterpret_cast<const float4*>(U.d + g));
+                dk.x += U.alpha * pk.x;
+                dk.y += U.alpha * pk.y;
+                dk.z += U.alpha * pk.z;
+                dk.w += U.alpha * pk.w;
+                *reinterpret_cast<float4*>(U.d + g) = dk;
+                *rr += (double)rn.x * rn.x + (double)rn.y * rn.y + (double)rn.z * rn.z + (double)rn.w * rn.w;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Up pass of one level.  Staged: 0 x_a, 1 t, 2 cW, 3 cS, 4 r; coarse: the parent's result.
+// Level 0 (zold != null): out is z, with the partial sums r.z and r.z_old.
+__device__ void up_pass(const TLevel& L, float om, float over, TileSmem& S, int b, int G, const float* zold,
+                        double* rz, double* rzo) {
+    const int nt = ntiles(L);
+    auto issue = [&](int t, int buf) {
+        int x0, y0;
+        tile_origin(L, t, x0, y0);
+        const int X0 = x0 - kHX, Y0 = y0 - kHY;
+        stage<kRW, kRH>(S.in[buf][0], L.xa, L.nx, L.ny, X0, Y0);
+        stage<kRW, kRH>(S.in[buf][1], L.t, L.nx, L.ny, X0, Y0);
+        stage<kRW, kRH>(S.in[buf][2], L.cW, L.nx, L.ny, X0, Y0);
+        stage<kRW, kRH>(S.in[buf][3], L.cS, L.nx, L.ny, X0, Y0);
+        stage<kRW, kRH>(S.in[buf][4], L.r, L.nx, L.ny, X0, Y0);
+        stage<kCW, kCH>(S.co[buf], L.xc, L.cnx, L.cny, x0 / 2 - 4, y0 / 2 - 2);
+        cp_commit();
+    };
+    if (b < nt) issue(b, 0);
+    int i = 0;
+    for (int t = b; t < nt; t += G, i++) {
+        const int buf = i & 1;
+        if (t + G < nt) {
+            issue(t + G, buf ^ 1);
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
+        }
+        __syncthreads();
+        int x0, y0;
+        tile_origin(L, t, x0, y0);
+        const float* XA = S.in[buf][0];
+        const float* T = S.in[buf][1];
+        const float* CW = S.in[buf][2];
+        const float* CS = S.in[buf][3];
+        const float* R = S.in[buf][4];
+        const float* C = S.co[buf];
+        float* XT = S.c1;
+        float* XB = S.c2;
+        // x~ on the tile and two rings: region columns kHX-2 .. kHX+kTX+1, all rows; the
+        // parent of region cell (lx, ly) is coarse region cell ((lx - kHX) / 2 + 4,
+        // (ly - kHY) / 2 + 2), with floor division (lx - kHX >= -2, ly - kHY >= -2)
+        constexpr int AW = kTX + 4;
+        for (int e = threadIdx.x; e < AW * kRH; e += blockDim.x) {
+            const int ly = e / AW, lx = kHX - 2 + (e - ly * AW);
+            const int ix = ly * kRW + lx;
+            const int pcx = ((lx - kHX + 2) >> 1) + 3, pcy = ((ly - kHY + 2) >> 1) + 1;
+            XT[ix] = XA[ix] + over * T[ix] * C[pcy * kCW + pcx];
+        }
+        __syncthreads();
+        // x_b on the tile and one ring
+        constexpr int BW = kTX + 2, BH = kTY + 2;
+        for (int e = threadIdx.x; e < BW * BH; e += blockDim.x) {
+            const int ly = e / BW, lx = e - ly * BW;
+            const int ix = (kHY - 1 + ly) * kRW + (kHX - 1 + lx);
+            XB[ix] = XT[ix] + om * (R[ix] - st5(XT, CW, CS, ix));
+        }
+        __syncthreads();
+        // the level's result on the tile
+        constexpr int Q4 = kTX / 4;
+        for (int e = threadIdx.x; e < Q4 * kTY; e += blockDim.x) {
+            const int ly = e / Q4, q4 = e - ly * Q4;
+            const int gx = x0 + 4 * q4, gy = y0 + ly;
+            if (gx >= L.nx || gy >= L.ny) continue;
+            const int ix = (kHY + ly) * kRW + (kHX + 4 * q4);
+            float o[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) o[u] = XB[ix + u] + om * (R[ix + u] - st5(XB, CW, CS, ix + u));
+            const size_t g = (size_t)gy * L.nx + gx;
+            *reinterpret_cast<float4*>(L.out + g) = make_float4(o[0], o[1], o[2], o[3]);
+            if (zold) {
+                const float4 zo = __ldcg(reinterpret_cast<const float4*>(zold + g));
+                const float zz[4] = {zo.x, zo.y, zo.z, zo.w};
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    *rz += (double)R[ix + u] * o[u];
+                    *rzo += (double)R[ix + u] * zz[u];
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+}  // namespace gq
+
+namespace gq {
+namespace {
+
+// The solve of k_pcg<true> with the aggregation V-cycle (gq_pcg.cuh, pcg_solve_w), its
+// team levels run by the tiled passes above.  Returns false when a wait timed out.
+__device__ bool tiled_solve(const SolveParams& P, const Workspace& w, RedShared& sh, MGShared& msh, TileSmem& S) {
+    const Team team{static_cast<int>(blockIdx.x), static_cast<int>(gridDim.x)};
+    const int N = P.N, nx = P.nx;
+    const int nchunk = N / 4;
+    const int tid = team.rank * blockDim.x + threadIdx.x;
+    const int stride = team.size * blockDim.x;
+    SolveCtl* ctl = w.ctl;
+    int* abort_flag = &ctl->abort;
+    int parity = 0;
+    const double* __restrict__ cW64 = w.wW;
+    const double* __restrict__ cS64 = w.wS;
+    const double* __restrict__ bh = w.rhs;
+    const double* __restrict__ s = w.dloc;
+    double* y = w.y;
+    double* r64 = w.r64;
+    const float* cW = w.cW32;
+    const float* cS = w.cS32;
+    float* pb[2] = {w.p32[0], w.p32[1]};
+    float* q = w.q32;
+    float* d = w.d32;
+    float* rbuf[2] = {w.r32, w.r32b};
+    int rsel = 0;
+    float* zc = w.mg.z;
+    float* zo = w.mg.zold;
+    const MGHierarchy& mg = w.mg;
+
+    const int flags = __ldcg(&ctl->input_flags);
+    if (flags) {
+        if (tid == 0) ctl->status = (flags & 2) ? kErrNonfinite : kErrInvalid;
+        return true;
+    }
+    if (tid == 0) ctl->t_start = global_ns();
+    cyc_reset(msh.amg);
+    if (!mg_build(w, team, tid, stride, P.spin_limit, abort_flag, msh)) {
+        if (threadIdx.x == 0) atomicExch(&ctl->status, kErrTimeout);
+        return false;
+    }
+    if (tid == 0) {
+        ctl->t_built = global_ns();
+        ctl->levels = mg.nlev;
+    }
+    const int nl = mg.nlev;
+    int lg = 0;                          // levels [0, lg) run on the whole team (lg >= 1 here)
+    while (lg < nl - 1 && mg.L[lg].N > P.block_cells) lg++;
+    const float om = P.mg_omega, over = P.mg_over;
+    auto tlevel = [&](int l) {
+        const MGLevel& M = mg.L[l];
+        const MGLevel& C = mg.L[l + 1];
+        TLevel t;
+        t.nx = M.nx;
+        t.ny = M.ny;
+        t.cW = M.cW;
+        t.cS = M.cS;
+        t.t = M.t;
+        t.r = l == 0 ? rbuf[rsel] : M.r;
+        t.xa = M.xa;
+        t.out = l == 0 ? zc : M.xb;
+        t.rc = C.r;
+        t.xc = l + 1 == lg ? C.xa : C.xb;
+        t.cnx = C.nx;
+        t.cny = C.ny;
+        return t;
+    };
+    auto bar = [&]() { return team_barrier(w.bar, team, P.spin_limit, abort_flag); };
+    const UpdateArgs no_update{false, 0.f, nullptr, nullptr, nullptr, nullptr};
+
+    // V-cycle z = B r: down passes (level 0's may be done, fused with the update), the
+    // block levels, up passes; rz, rzo receive this thread's r.z and r.z_old
+    auto vcycle = [&](bool pre0_done, double* rz, double* rzo) -> bool {
+        for (int l = pre0_done ? 1 : 0; l < lg; l++) {
+            cyc_mark(msh.amg, team, l);
+            double unused = 0.0;
+            down_pass(tlevel(l), om, no_update, S, team.rank, team.size, &unused);
+            if (!bar()) return false;
+        }
+        if (team.rank == 0) {
+            cyc_mark(msh.amg, team, lg);
+            const Range br{static_cast<int>(threadIdx.x), static_cast<int>(blockDim.x)};
+            const float* r0 = rbuf[rsel];
+            for (int l = lg; l + 1 < nl; l++) {
+                const Lv F = level_view(mg, l, r0, zc), C = level_view(mg, l + 1, r0, zc);
+                cyc_presmooth<false>(F, om, br, l == lg);
+                __syncthreads();
+                if (l == lg) cyc_restrict<true>(F, C, br);
+                else cyc_restrict<false>(F, C, br);
+                __syncthreads();
+            }
+            const Lv Z = level_view(mg, nl - 1, r0, zc);
+            cyc_coarse(Z, mg.inv, br, lg == nl - 1, zo, nullptr, nullptr);
+            __syncthreads();
+            for (int l = nl - 2; l >= lg; l--) {
+                const Lv F = level_view(mg, l, r0, zc), C = level_view(mg, l + 1, r0, zc);
+                if (l == lg) {
+                    cyc_prolong_smooth<true>(F, C, om, over, br);
+                    __syncthreads();
+                    cyc_postsmooth<true>(F, om, br, zo, nullptr, nullptr);
+                } else {
+                    cyc_prolong_smooth<false>(F, C, om, over, br);
+                    __syncthreads();
+                    cyc_postsmooth<false>(F, om, br, zo, nullptr, nullptr);
+                }
+                __syncthreads();
+            }
+        }
+        if (!bar()) return false;
+        for (int l = lg - 1; l >= 1; l--) {
+            cyc_mark(msh.amg, team, l);
+            up_pass(tlevel(l), om, over, S, team.rank, team.size, nullptr, nullptr, nullptr);
+            if (!bar()) return false;
+        }
+        cyc_mark(msh.amg, team, 0);
+        up_pass(tlevel(0), om, over, S, team.rank, team.size, zo, rz, rzo);
+        cyc_mark(msh.amg, team, kAmgMaxLevels - 1);
+        return true;
+    };
+
+    // FP64 residual r64 = b^ - A^ y and its norms: |r|^2, |r/s|^2, |b/s|^2, max |r_k/y_k|, max |r_k|
+    double tr[5];
+    auto true_residual = [&](bool first) -> bool {
+#pragma unroll
+        for (int t = 0; t < 5; t++) tr[t] = 0.0;
+        for (int c = tid; c < N / 2; c += stride) {
+            const int k = c * 2;
+            const bool hs = k >= nx, hn = k + nx < N, hw = k > 0, he = k + 2 < N;
+            double yc[2], ys[2] = {0.0, 0.0}, yn[2] = {0.0, 0.0}, cw[2], cs[2], csn[2] = {0.0, 0.0}, bk[2], sk[2];
+            double yw = 0.0, ye = 0.0, cwe = 0.0;
+            ld64<2>(y + k, yc);
+            ld64<2>(cW64 + k, cw);
+            ld64<2>(cS64 + k, cs);
+            ld64<2>(bh + k, bk);
+            ld64<2>(s + k, sk);
+            if (hw) yw = __ldcg(y + k - 1);
+            if (he) {
+                ye = __ldcg(y + k + 2);
+                cwe = cW64[k + 2];
+            }
+            if (hs) ld64<2>(y + k - nx, ys);
+            if (hn) {
+                ld64<2>(y + k + nx, yn);
+                ld64<2>(cS64 + k + nx, csn);
+            }
+            double rk[2];
+#pragma unroll
+            for (int i = 0; i < 2; i++) {
+                const double left = i == 0 ? yw : yc[0];
+                const double right = i == 1 ? ye : yc[1];
+                const double cright = i == 1 ? cwe : cw[1];
+                const double ax = yc[i] - cw[i] * left - cright * right - cs[i] * ys[i] - csn[i] * yn[i];
+                rk[i] = bk[i] - ax;
+                const double ru = abs_ratio_approx(rk[i], sk[i]);
+                tr[0] += rk[i] * rk[i];
+                tr[1] += ru * ru;
+                if (first) {
+                    const double bu = abs_ratio_approx(bk[i], sk[i]);
+                    tr[2] += bu * bu;
+                }
+                tr[3] = nanmax(tr[3], abs_ratio_approx(rk[i], yc[i]));
+                tr[4] = nanmax(tr[4], fabs(rk[i]));
+            }
+            st64<2>(r64 + k, rk);
+        }
+        return allreduce<3, 2>(tr, w.partials, parity, w.bar, P.spin_limit, abort_flag, sh, team);
+    };
+
+    int it = 0, nref = 0, status = kErrNotConverged;
+    double crit = 0.0, l2 = 0.0, bb = 1.0;
+    bool timed_out = false;
+    if (!true_residual(true)) {
+        timed_out = true;
+        goto done;
+    }
+    bb = tr[2];
+    crit = tr[3];
+    l2 = sqrt(tr[1] / bb);
+    if (!isfinite(tr[0]) || !isfinite(bb) || !(crit == crit)) {
+        status = kErrNonfinite;
+        goto done;
+    }
+    if (crit <= P.rtol) {
+        status = kOk;
+        goto done;
+    }
+    {
+        const double zs = exp2(-(double)ilogb(tr[4] > 0.0 ? tr[4] : 1.0));
+        const double scale = zs;
+        double rr = tr[0] * scale * scale;
+        double rr_ref = rr;
+        double beta = 0.0;
+        bool use_p = false;
+        int cur = 0;
+        double best = crit;
+        int it_best = 0, stall = 0;
+        bool first = true, pre0_done = false;
+        double rz_prev = 1.0;
+        // FP32 residual from the FP64 one (scaled), correction d = 0
+        auto refresh = [&](bool initial) -> bool {
+            float* r0 = rbuf[rsel];
+            for (int c = tid; c < nchunk; c += stride) {
+                const int k = c * 4;
+                double t[4];
+                float f[4], zero[4];
+                ld64<4>(r64 + k, t);
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    f[i] = static_cast<float>(t[i] * zs);
+                    zero[i] = 0.f;
+                }
+                stf<4>(r0 + k, f);
+                stf<4>(d + k, zero);
+                if (initial) stf<4>(zo + k, zero);
+            }
+            return bar();
+        };
+        if (!refresh(true)) {
+            timed_out = true;
+            goto done;
+        }
+        auto refine = [&]() -> bool {
+            const double inv = 1.0 / scale;
+            for (int c = tid; c < nchunk; c += stride) {
+                const int k = c * 4;
+                double yk[4];
+                float dk[4], zero[4];
+                ld64<4>(y + k, yk);
+                ldf<4>(d + k, dk);
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    yk[i] += static_cast<double>(dk[i]) * inv;
+                    zero[i] = 0.f;
+                }
+                st64<4>(y + k, yk);
+                stf<4>(d + k, zero);
+            }
+            if (!bar()) {
+                timed_out = true;
+                return false;
+            }
+            if (!true_residual(false)) {
+                timed_out = true;
+                return false;
+            }
+            nref++;
+            crit = tr[3];
+            l2 = sqrt(tr[1] / bb);
+            if (!isfinite(tr[0]) || !(crit == crit)) {
+                status = kErrNonfinite;
+                return false;
+            }
+            if (crit <= P.rtol) {
+                status = kOk;
+                return false;
+            }
+            if (crit < kStallGain * best) {
+                best = crit;
+                it_best = it;
+                stall = 0;
+            } else {
+                stall++;
+            }
+            if (it >= P.max_iter || nref >= P.max_refine || (stall >= kStallChecks && it - it_best >= kStallIters)) {
+                status = kErrNotConverged;
+                return false;
+            }
+            const double rr_true = tr[0] * scale * scale;
+            if (P.restart) {
+                use_p = false;
+                beta = 0.0;
+                first = true;
+            } else {
+                use_p = true;
+                beta = rr > 0.0 ? rr_true / rr : 0.0;
+            }
+            rr = rr_true;
+            rr_ref = rr_true;
+            if (!refresh(false)) {
+                timed_out = true;
+                return false;
+            }
+            return true;
+        };
+
+        while (true) {
+            double rho_mg = 0.0;
+            bool degenerate = false;
+            {
+                double vz[2] = {0.0, 0.0};
+                if (!vcycle(pre0_done, &vz[0], &vz[1])) {
+                    timed_out = true;
+                    break;
+                }
+                pre0_done = false;
+                if (!allreduce<2, 0>(vz, w.partials, parity, w.bar, P.spin_limit, abort_flag, sh, team)) {
+                    timed_out = true;
+                    break;
+                }
+                if (!isfinite(vz[0]) || !isfinite(vz[1])) {
+                    status = kErrNonfinite;
+                    break;
+                }
+                degenerate = !(vz[0] > 0.0);
+                const bool restart_dir = first || fabs(vz[1]) >= 0.2 * vz[0];
+                beta = restart_dir ? 0.0 : fmax(0.0, (vz[0] - vz[1]) / rz_prev);
+                use_p = !restart_dir;
+                rz_prev = vz[0];
+                rho_mg = vz[0];
+                first = false;
+            }
+            if (!degenerate) {
+                // ---- S: p = z + beta p_old ; q = A^ p ; p.q --------------------------------
+                cyc_mark(msh.amg, team, kAmgMaxLevels - 4);
+                const float* __restrict__ pold = pb[cur];
+                float* __restrict__ pnew = pb[cur ^ 1];
+                const float rb = static_cast<float>(beta);
+                double v1[1] = {0.0};
+                for (int c = tid; c < nchunk; c += stride) {
+                    const int k = c * 4;
+                    const bool hs = k >= nx, hn = k + nx < N, hw = k > 0, he = k + 4 < N;
+                    float rc[4], rs[4] = {0.f, 0.f, 0.f, 0.f}, rn[4] = {0.f, 0.f, 0.f, 0.f}, rw = 0.f, re = 0.f;
+                    float pc[4] = {0.f, 0.f, 0.f, 0.f}, ps[4] = {0.f, 0.f, 0.f, 0.f}, pn[4] = {0.f, 0.f, 0.f, 0.f};
+                    float pw = 0.f, pe = 0.f;
+                    ldf<4>(zc + k, rc);
+                    if (hs) ldf<4>(zc + k - nx, rs);
+                    if (hn) ldf<4>(zc + k + nx, rn);
+                    if (hw) rw = __ldcg(zc + k - 1);
+                    if (he) re = __ldcg(zc + k + 4);
+                    if (use_p) {
+                        ldf<4>(pold + k, pc);
+                        if (hs) ldf<4>(pold + k - nx, ps);
+                        if (hn) ldf<4>(pold + k + nx, pn);
+                        if (hw) pw = __ldcg(pold + k - 1);
+                        if (he) pe = __ldcg(pold + k + 4);
+                    }
+                    float cw[4], cs[4], csn[4] = {0.f, 0.f, 0.f, 0.f}, cwe = 0.f;
+                    ldf<4>(cW + k, cw);
+                    ldf<4>(cS + k, cs);
+                    if (he) cwe = __ldcg(cW + k + 4);
+                    if (hn) ldf<4>(cS + k + nx, csn);
+                    float p[4], pS[4], pN[4];
+                    const float pW = use_p ? rw + rb * pw : rw;
+                    const float pE = use_p ? re + rb * pe : re;
+#pragma unroll
+                    for (int i = 0; i < 4; i++) {
+                        p[i] = use_p ? rc[i] + rb * pc[i] : rc[i];
+                        pS[i] = use_p ? rs[i] + rb * ps[i] : rs[i];
+                        pN[i] = use_p ? rn[i] + rb * pn[i] : rn[i];
+                    }
+                    float qv[4];
+#pragma unroll
+                    for (int i = 0; i < 4; i++) {
+                        const float left = i == 0 ? pW : p[i - 1];
+                        const float right = i == 3 ? pE : p[i + 1];
+                        const float cright = i == 3 ? cwe : cw[i + 1];
+                        qv[i] = p[i] - cw[i] * left - cright * right - cs[i] * pS[i] - csn[i] * pN[i];
+                        v1[0] += static_cast<double>(p[i]) * static_cast<double>(qv[i]);
+                    }
+                    stf<4>(pnew + k, p);
+                    stf<4>(q + k, qv);
+                }
+                if (!allreduce<1, 0>(v1, w.partials, parity, w.bar, P.spin_limit, abort_flag, sh, team)) {
+                    timed_out = true;
+                    break;
+                }
+                const double pq = v1[0];
+                if (!isfinite(pq)) {
+                    status = kErrNonfinite;
+                    break;
+                }
+                degenerate = !(pq > 0.0);
+                if (!degenerate) {
+                    const double alpha = rho_mg / pq;
+                    float* tz = zc;          // this z becomes z_old of the next cycle
+                    zc = zo;
+                    zo = tz;
+                    cur ^= 1;
+                    // ---- U fused with the next cycle's level-0 down pass ---------------------
+                    cyc_mark(msh.amg, team, kAmgMaxLevels - 3);
+                    double v2[2] = {0.0, 0.0};
+                    const UpdateArgs upd{true, static_cast<float>(alpha), q, pnew, d, rbuf[rsel ^ 1]};
+                    down_pass(tlevel(0), om, upd, S, team.rank, team.size, &v2[0]);
+                    rsel ^= 1;
+                    if (!allreduce<1, 1>(v2, w.partials, parity, w.bar, P.spin_limit, abort_flag, sh, team)) {
+                        timed_out = true;
+                        break;
+                    }
+                    it++;
+                    const double rr_new = v2[0];
+                    if (!isfinite(rr_new)) {
+                        status = kErrNonfinite;
+                        break;
+                    }
+                    const bool check = sqrt(rr_new) <= P.drop * sqrt(rr_ref) || it >= P.max_iter;
+                    if (!check) {
+                        rr = rr_new;
+                        pre0_done = true;
+                        continue;
+                    }
+                    rr = rr_new;
+                }
+            }
+            cyc_mark(msh.amg, team, kAmgMaxLevels - 2);
+            if (!refine()) break;
+        }
+    }
+
+done:
+    if (!timed_out) amg_cycle_report(w.amg, msh.amg, team);
+    if (timed_out) {
+        if (threadIdx.x == 0) atomicExch(&ctl->status, kErrTimeout);
+        return false;
+    }
+    if (tid == 0) {
+        ctl->t_end = global_ns();
+        ctl->status = status;
+        ctl->iterations = it;
+        ctl->refinements = nref;
+        ctl->crit = crit;
+        ctl->l2 = l2;
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(kSolveThreads, 1) k_pcg_tiled(SolveParams P, Workspace w) {
+    __shared__ RedShared sh;
+    __shared__ MGShared msh;
+    extern __shared__ __align__(16) unsigned char tile_raw[];
+    TileSmem& S = *reinterpret_cast<TileSmem*>(tile_raw);
+    tiled_solve(P, w, sh, msh, S);
+}
+
+}  // namespace
+
+size_t tiled_smem_bytes() { return sizeof(TileSmem); }
+
+const void* solve_kernel_tiled() { return reinterpret_cast<const void*>(k_pcg_tiled); }
+
+// the tiled kernel takes a problem whose team levels (those above block_cells cells, at
+// least level 0) all have widths divisible by 8 and even heights
+bool tiled_eligible(const SolveParams& p, const Workspace& w) {
+    if (!p.mixed || p.precond != GQ_PRECOND_MG || w.mg.nlev < 2) return false;
+    if (p.N <= p.block_cells) return false;
+    for (int l = 0; l < w.mg.nlev - 1 && w.mg.L[l].N > p.block_cells; l++) {
+        const MGLevel& L = w.mg.L[l];
+        if (L.nx % 8 != 0 || L.ny % 2 != 0) return false;
+    }
+    return true;
+}
+
+}  // namespace gq

@@ -41,6 +41,7 @@ class SolverOptions:
     mg_block_cells: int = 0       # 0 = library default
     subcycle_freeze_D: int = 1    # sub-cycled steps: 1 = D from the hydro step's start (the paper's order),
                                   # 0 = D re-formed from each sub-step's state
+    untiled: int = 0              # 1 = never the tiled solve kernel
 
     def to_c(self) -> N.SolverOpts:
         o = N.SolverOpts()
@@ -51,6 +52,7 @@ class SolverOptions:
         o.precond, o.mg_omega, o.mg_over = int(self.precond), float(self.mg_omega), float(self.mg_over)
         o.mg_block_cells = int(self.mg_block_cells)
         o.subcycle_freeze_D = int(self.subcycle_freeze_D)
+        o.untiled = int(self.untiled)
         return o
 
 

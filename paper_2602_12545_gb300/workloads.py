@@ -180,7 +180,9 @@ def batch_sizes(n_problems: int = 256, seed: int = 1003):
 def config3(n_problems: int = 256, seed: int = 1003, max_side: Optional[int] = None) -> List[FLDProblem]:
     """256 independent problems, nx, ny log-uniform in [32, 512], alternating Cartesian
     (dx = 1e12, reflecting) and spherical-polar (r log-spaced 1e11..1e14, theta 0..pi,
-    Milne at outer r), i.i.d. config-0 fields, dt = 10^U(3,6) s, mixed precision to 1e-8.
+    Milne at outer r), i.i.d. config-0 fields, dt = 10^U(3,6) s, mixed precision with a
+    cell-wise residual of 1e-10, which keeps every cell of every problem within 1e-8 of
+    the oracle (a residual of 1e-8 leaves errors up to 2e-7 on some spherical draws).
     Problem p draws its fields from seed + 1 + p."""
     nxs, nys, dts = batch_sizes(n_problems, seed)
     out = []
@@ -193,11 +195,11 @@ def config3(n_problems: int = 256, seed: int = 1003, max_side: Optional[int] = N
         if p % 2 == 0:
             xf, yf = uniform_faces(nx, 1e12), uniform_faces(ny, 1e12)
             pr = _pack(f"c3_p{p}_cart{nx}x{ny}", CARTESIAN, xf, yf, rho, T, Trad, dts[p],
-                       bc=(BC_REFLECT,) * 4, precision=PREC_MIXED, rtol=1e-8)
+                       bc=(BC_REFLECT,) * 4, precision=PREC_MIXED, rtol=1e-10)
         else:
             xf, yf = log_faces(nx, 1e11, 1e14), theta_faces(ny)
             pr = _pack(f"c3_p{p}_sph{nx}x{ny}", SPHERICAL, xf, yf, rho, T, Trad, dts[p],
-                       bc=(BC_REFLECT, BC_MILNE, BC_REFLECT, BC_REFLECT), precision=PREC_MIXED, rtol=1e-8)
+                       bc=(BC_REFLECT, BC_MILNE, BC_REFLECT, BC_REFLECT), precision=PREC_MIXED, rtol=1e-10)
         out.append(pr)
     return out
 
@@ -224,13 +226,14 @@ def config4_trace(n_requests: int = 2000, rate_per_s: float = 2000.0, seed: int 
 
 def serve_problem(req: ServeRequest) -> FLDProblem:
     """A serving request's initial state: uniform Cartesian square grid, dx = 1e12 cm,
-    config-0 fields, dt = 1e4 s, reflecting, mixed precision to 1e-8."""
+    config-0 fields, dt = 1e4 s, reflecting, mixed precision with a cell-wise residual of
+    1e-10 (each step within 1e-8 of the oracle)."""
     n = req.side
     rng = np.random.default_rng(req.seed)
     rho, T, Trad = _fields_iid(n, n, rng)
     f = uniform_faces(n, 1e12)
     return _pack(f"c4_r{req.rid}_cart{n}", CARTESIAN, f, f.copy(), rho, T, Trad, 1e4,
-                 bc=(BC_REFLECT,) * 4, precision=PREC_MIXED, rtol=1e-8)
+                 bc=(BC_REFLECT,) * 4, precision=PREC_MIXED, rtol=1e-10)
 
 
 def random_small(nx: int, ny: int, coord: int, bc, seed: int, limiter: int = LIMITER_LP,
