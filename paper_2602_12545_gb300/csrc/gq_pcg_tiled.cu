@@ -40,14 +40,31 @@ constexpr int kNR = kRW * kRH;
 constexpr int kCW = kTX / 2 + 8;       // staged coarse region (40 x 12)
 constexpr int kCH = kTY / 2 + 4;
 constexpr int kNC = kCW * kCH;
-constexpr int kStaged = 5;             // staged arrays per tile
+constexpr int kNT = kTX * kTY;         // cells of a tile
+constexpr int kStaged = 5;             // staged arrays with a halo
+constexpr int kOwn = 2;                // staged arrays of the tile alone
+constexpr int kNst = 3;                // pipeline depth: tiles staged ahead of the one computed
+
+constexpr int kBlkCap = 1536;          // cells of the block levels kept in shared memory
+
+// The levels one block runs (at most block_cells cells each, coarsened to the dense
+// coarsest one): their couplings, transfer weights and coarsest inverse stay in shared
+// memory for the whole solve, so that each of their passes costs a block barrier and no
+// global-memory round trip.
+struct BlockLevels {
+    float cw[kBlkCap], cs[kBlkCap], t[kBlkCap];
+    float inv[kCoarseMax * kCoarseMax];
+};
 
 struct TileSmem {
-    float in[2][kStaged][kNR];         // staged inputs, two buffers
-    float co[2][kNC];                  // staged coarse values (up passes)
+    float in[kNst][kStaged][kNR];      // staged inputs with a halo (block levels: their vectors)
+    float co[kNst][kNC];               // staged coarse values (up passes)
+    float own[kNst][kOwn][kNT];        // staged inputs of the tile alone
     float c1[kNR];                     // computed: x_a (down) or x~ (up)
     float c2[kNR];                     // computed: x_b (up)
+    BlockLevels blk;
 };
+static_assert(3 * kBlkCap <= kNst * kStaged * kNR, "block-level vectors must fit the staging buffers");
 
 __device__ __forceinline__ void cp16(float* dst, const float* src, bool ok) {
     const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
@@ -99,6 +116,31 @@ __device__ __forceinline__ void tile_origin(const TLevel& L, int t, int& x0, int
     y0 = ty * kTY;
 }
 
+// The tiles b, b + G, b + 2G, ... of a pass, each staged kNst - 1 tiles ahead of its
+// arithmetic: issue(t, buf) enqueues tile t's copies into buffer buf, compute(t, buf)
+// works on it.  One commit group per tile (empty ones included), so that waiting for
+// all but the newest kNst - 1 groups means the oldest tile has landed.
+template <class Issue, class Compute>
+__device__ __forceinline__ void tile_loop(int nt, int b, int G, Issue issue, Compute compute) {
+#pragma unroll
+    for (int k = 0; k < kNst - 1; k++) {
+        const int t = b + k * G;
+        if (t < nt) issue(t, k);
+        cp_commit();
+    }
+    int i = 0;
+    for (int t = b; t < nt; t += G, i++) {
+        const int tn = t + (kNst - 1) * G;
+        if (tn < nt) issue(tn, (i + kNst - 1) % kNst);
+        cp_commit();
+        cp_wait<kNst - 1>();
+        __syncthreads();
+        compute(t, i % kNst);
+        __syncthreads();
+    }
+    cp_wait<0>();
+}
+
 // Kernel-wide arguments of the fused level-0 down pass: the Krylov update.
 struct UpdateArgs {
     bool on;                   // false: plain down pass on r
@@ -110,31 +152,27 @@ struct UpdateArgs {
 };
 
 // Down pass of one level over all of its tiles this block owns (tiles b, b + G, ...).
-// Staged: 0 r (or r_old), 1 q (update only), 2 cW, 3 cS, 4 t.
+// Staged with a halo: 0 r (or r_old), 1 q (update only), 2 cW, 3 cS, 4 t; the tile
+// alone: 0 p, 1 d (update only).
 __device__ void down_pass(const TLevel& L, float om, const UpdateArgs& U, TileSmem& S, int b, int G, double* rr) {
-    const int nt = ntiles(L);
+    // this thread's r'.r' over its cells of the pass, in FP32 (a few dozen terms; FP64
+    // arithmetic per cell would cost more than the pass's memory traffic on this part)
+    float rrf = 0.f;
     auto issue = [&](int t, int buf) {
         int x0, y0;
         tile_origin(L, t, x0, y0);
         const int X0 = x0 - kHX, Y0 = y0 - kHY;
         stage<kRW, kRH>(S.in[buf][0], L.r, L.nx, L.ny, X0, Y0);
-        if (U.on) stage<kRW, kRH>(S.in[buf][1], U.q, L.nx, L.ny, X0, Y0);
         stage<kRW, kRH>(S.in[buf][2], L.cW, L.nx, L.ny, X0, Y0);
         stage<kRW, kRH>(S.in[buf][3], L.cS, L.nx, L.ny, X0, Y0);
         stage<kRW, kRH>(S.in[buf][4], L.t, L.nx, L.ny, X0, Y0);
-        cp_commit();
-    };
-    if (b < nt) issue(b, 0);
-    int i = 0;
-    for (int t = b; t < nt; t += G, i++) {
-        const int buf = i & 1;
-        if (t + G < nt) {
-            issue(t + G, buf ^ 1);
-            cp_wait<1>();
-        } else {
-            cp_wait<0>();
+        if (U.on) {
+            stage<kRW, kRH>(S.in[buf][1], U.q, L.nx, L.ny, X0, Y0);
+            stage<kTX, kTY>(S.own[buf][0], U.p, L.nx, L.ny, x0, y0);
+            stage<kTX, kTY>(S.own[buf][1], U.d, L.nx, L.ny, x0, y0);
         }
-        __syncthreads();
+    };
+    auto compute = [&](int t, int buf) {
         int x0, y0;
         tile_origin(L, t, x0, y0);
         float* R = S.in[buf][0];
@@ -171,37 +209,32 @@ __device__ void down_pass(const TLevel& L, float om, const UpdateArgs& U, TileSm
             const int gi = x0 / 2 + ci, gj = y0 / 2 + cj;
             if (gi < L.cnx && gj < L.cny) L.rc[(size_t)gj * L.cnx + gi] = acc;
         }
-        // the tile's x_a (and, fused with the update, r', d and r'.r')
-        constexpr int Q4 = kTX / 4;
-        for (int e = threadIdx.x; e < Q4 * kTY; e += blockDim.x) {
-            const int ly = e / Q4, q4 = e - ly * Q4;
-            const int gx = x0 + 4 * q4, gy = y0 + ly;
+        // the tile's x_a (and, fused with the update, r', d and r'.r'), one cell a thread
+        for (int e = threadIdx.x; e < kNT; e += blockDim.x) {
+            const int ly = e / kTX, lx = e - ly * kTX;
+            const int gx = x0 + lx, gy = y0 + ly;
             if (gx >= L.nx || gy >= L.ny) continue;
-            const int ix = (kHY + ly) * kRW + (kHX + 4 * q4);
+            const int ix = (kHY + ly) * kRW + (kHX + lx);
             const size_t g = (size_t)gy * L.nx + gx;
-            *reinterpret_cast<float4*>(L.xa + g) = make_float4(XA[ix], XA[ix + 1], XA[ix + 2], XA[ix + 3]);
+            L.xa[g] = XA[ix];
             if (U.on) {
-                const float4 rn = make_float4(R[ix], R[ix + 1], R[ix + 2], R[ix + 3]);
-                *reinterpret_cast<float4*>(U.rnew + g) = rn;
-                const float4 pk = __ldcg(reinterpret_cast<const float4*>(U.p + g));
-                float4 dk = __ldcg(reinterpret_cast<const float4*>(U.d + g));
-                dk.x += U.alpha * pk.x;
-                dk.y += U.alpha * pk.y;
-                dk.z += U.alpha * pk.z;
-                dk.w += U.alpha * pk.w;
-                *reinterpret_cast<float4*>(U.d + g) = dk;
-                *rr += (double)rn.x * rn.x + (double)rn.y * rn.y + (double)rn.z * rn.z + (double)rn.w * rn.w;
+                const float rn = R[ix];
+                U.rnew[g] = rn;
+                U.d[g] = S.own[buf][1][e] + U.alpha * S.own[buf][0][e];
+                rrf += rn * rn;
             }
         }
-        __syncthreads();
-    }
+    };
+    tile_loop(ntiles(L), b, G, issue, compute);
+    *rr += static_cast<double>(rrf);
 }
 
-// Up pass of one level.  Staged: 0 x_a, 1 t, 2 cW, 3 cS, 4 r; coarse: the parent's result.
-// Level 0 (zold != null): out is z, with the partial sums r.z and r.z_old.
+// Up pass of one level.  Staged with a halo: 0 x_a, 1 t, 2 cW, 3 cS, 4 r; coarse: the
+// parent's result; the tile alone: 0 z_old (level 0).  Level 0 (zold != null): out is z,
+// with the partial sums r.z and r.z_old.
 __device__ void up_pass(const TLevel& L, float om, float over, TileSmem& S, int b, int G, const float* zold,
                         double* rz, double* rzo) {
-    const int nt = ntiles(L);
+    float rzf = 0.f, rzof = 0.f;       // this thread's partial sums (FP32, see down_pass)
     auto issue = [&](int t, int buf) {
         int x0, y0;
         tile_origin(L, t, x0, y0);
@@ -212,19 +245,9 @@ __device__ void up_pass(const TLevel& L, float om, float over, TileSmem& S, int 
         stage<kRW, kRH>(S.in[buf][3], L.cS, L.nx, L.ny, X0, Y0);
         stage<kRW, kRH>(S.in[buf][4], L.r, L.nx, L.ny, X0, Y0);
         stage<kCW, kCH>(S.co[buf], L.xc, L.cnx, L.cny, x0 / 2 - 4, y0 / 2 - 2);
-        cp_commit();
+        if (zold) stage<kTX, kTY>(S.own[buf][0], zold, L.nx, L.ny, x0, y0);
     };
-    if (b < nt) issue(b, 0);
-    int i = 0;
-    for (int t = b; t < nt; t += G, i++) {
-        const int buf = i & 1;
-        if (t + G < nt) {
-            issue(t + G, buf ^ 1);
-            cp_wait<1>();
-        } else {
-            cp_wait<0>();
-        }
-        __syncthreads();
+    auto compute = [&](int t, int buf) {
         int x0, y0;
         tile_origin(L, t, x0, y0);
         const float* XA = S.in[buf][0];
@@ -254,29 +277,24 @@ __device__ void up_pass(const TLevel& L, float om, float over, TileSmem& S, int 
             XB[ix] = XT[ix] + om * (R[ix] - st5(XT, CW, CS, ix));
         }
         __syncthreads();
-        // the level's result on the tile
-        constexpr int Q4 = kTX / 4;
-        for (int e = threadIdx.x; e < Q4 * kTY; e += blockDim.x) {
-            const int ly = e / Q4, q4 = e - ly * Q4;
-            const int gx = x0 + 4 * q4, gy = y0 + ly;
+        // the level's result on the tile, one cell a thread
+        for (int e = threadIdx.x; e < kNT; e += blockDim.x) {
+            const int ly = e / kTX, lx = e - ly * kTX;
+            const int gx = x0 + lx, gy = y0 + ly;
             if (gx >= L.nx || gy >= L.ny) continue;
-            const int ix = (kHY + ly) * kRW + (kHX + 4 * q4);
-            float o[4];
-#pragma unroll
-            for (int u = 0; u < 4; u++) o[u] = XB[ix + u] + om * (R[ix + u] - st5(XB, CW, CS, ix + u));
-            const size_t g = (size_t)gy * L.nx + gx;
-            *reinterpret_cast<float4*>(L.out + g) = make_float4(o[0], o[1], o[2], o[3]);
+            const int ix = (kHY + ly) * kRW + (kHX + lx);
+            const float o = XB[ix] + om * (R[ix] - st5(XB, CW, CS, ix));
+            L.out[(size_t)gy * L.nx + gx] = o;
             if (zold) {
-                const float4 zo = __ldcg(reinterpret_cast<const float4*>(zold + g));
-                const float zz[4] = {zo.x, zo.y, zo.z, zo.w};
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    *rz += (double)R[ix + u] * o[u];
-                    *rzo += (double)R[ix + u] * zz[u];
-                }
+                rzf += R[ix] * o;
+                rzof += R[ix] * S.own[buf][0][e];
             }
         }
-        __syncthreads();
+    };
+    tile_loop(ntiles(L), b, G, issue, compute);
+    if (zold) {
+        *rz += static_cast<double>(rzf);
+        *rzo += static_cast<double>(rzof);
     }
 }
 
@@ -352,6 +370,28 @@ __device__ bool tiled_solve(const SolveParams& P, const Workspace& w, RedShared&
         return t;
     };
     auto bar = [&]() { return team_barrier(w.bar, team, P.spin_limit, abort_flag); };
+    // block levels held in shared memory when they fit (first cell of each level there)
+    int blk_off[kAmgMaxLevels];
+    int blk_total = 0;
+    for (int l = lg; l < nl && l - lg < kAmgMaxLevels; l++) {
+        blk_off[l - lg] = blk_total;
+        blk_total += mg.L[l].N;
+    }
+    const bool blk_smem = blk_total <= kBlkCap && mg.L[nl - 1].N <= kCoarseMax;
+    if (blk_smem && team.rank == 0) {
+        for (int l = lg; l < nl; l++) {
+            const MGLevel& M = mg.L[l];
+            const int o = blk_off[l - lg];
+            for (int k = threadIdx.x; k < M.N; k += blockDim.x) {
+                S.blk.cw[o + k] = __ldcg(M.cW + k);
+                S.blk.cs[o + k] = __ldcg(M.cS + k);
+                S.blk.t[o + k] = l + 1 < nl ? __ldcg(M.t + k) : 0.f;
+            }
+        }
+        const int nc = mg.L[nl - 1].N;
+        for (int e = threadIdx.x; e < nc * nc; e += blockDim.x) S.blk.inv[e] = __ldcg(mg.inv + e);
+        __syncthreads();
+    }
     const UpdateArgs no_update{false, 0.f, nullptr, nullptr, nullptr, nullptr};
 
     // V-cycle z = B r: down passes (level 0's may be done, fused with the update), the
@@ -363,7 +403,49 @@ __device__ bool tiled_solve(const SolveParams& P, const Workspace& w, RedShared&
             down_pass(tlevel(l), om, no_update, S, team.rank, team.size, &unused);
             if (!bar()) return false;
         }
-        if (team.rank == 0) {
+        if (team.rank == 0 && blk_smem) {
+            // the block levels in shared memory: right-hand side of level lg from the team,
+            // the cycle below it, the result of level lg back to global memory
+            cyc_mark(msh.amg, team, lg);
+            const Range br{static_cast<int>(threadIdx.x), static_cast<int>(blockDim.x)};
+            float* vr = &S.in[0][0][0];
+            float* vxa = vr + kBlkCap;
+            float* vxb = vxa + kBlkCap;
+            for (int k = threadIdx.x; k < mg.L[lg].N; k += blockDim.x) vr[k] = __ldcg(mg.L[lg].r + k);
+            __syncthreads();
+            auto view = [&](int l) {
+                const int o = blk_off[l - lg];
+                Lv v;
+                v.nx = mg.L[l].nx;
+                v.ny = mg.L[l].ny;
+                v.N = mg.L[l].N;
+                v.cW = S.blk.cw + o;
+                v.cS = S.blk.cs + o;
+                v.t = S.blk.t + o;
+                v.r = vr + o;
+                v.xa = vxa + o;
+                v.xb = vxb + o;
+                v.out = vxa + o;
+                return v;
+            };
+            for (int l = lg; l + 1 < nl; l++) {
+                const Lv F = view(l), C = view(l + 1);
+                cyc_presmooth<false>(F, om, br, false);
+                __syncthreads();
+                cyc_restrict<false>(F, C, br);
+                __syncthreads();
+            }
+            cyc_coarse(view(nl - 1), S.blk.inv, br, false, nullptr, nullptr, nullptr);
+            __syncthreads();
+            for (int l = nl - 2; l >= lg; l--) {
+                const Lv F = view(l), C = view(l + 1);
+                cyc_prolong_smooth<false>(F, C, om, over, br);
+                __syncthreads();
+                cyc_postsmooth<false>(F, om, br, nullptr, nullptr, nullptr);
+                __syncthreads();
+            }
+            for (int k = threadIdx.x; k < mg.L[lg].N; k += blockDim.x) mg.L[lg].xa[k] = vxa[k];
+        } else if (team.rank == 0) {
             cyc_mark(msh.amg, team, lg);
             const Range br{static_cast<int>(threadIdx.x), static_cast<int>(blockDim.x)};
             const float* r0 = rbuf[rsel];
@@ -525,13 +607,56 @@ __device__ bool tiled_solve(const SolveParams& P, const Workspace& w, RedShared&
                 timed_out = true;
                 return false;
             }
-            if (!true_residual(false)) {
-                timed_out = true;
-                return false;
+            // the FP64 residual b^ - A^ y, written straight to the FP32 Krylov residual
+            // (times the fixed scale zs), with its FP32 square sum and the cell-wise
+            // criterion: the only FP64 arithmetic per cell is the stencil, the scaling
+            // and the criterion's quotient (this part's FP64 rate is a sixtieth of FP32)
+            {
+                float rrf = 0.f;
+                double cr[2] = {0.0, 0.0};
+                float* r0 = rbuf[rsel];
+                for (int c = tid; c < N / 2; c += stride) {
+                    const int k = c * 2;
+                    const bool hs = k >= nx, hn = k + nx < N, hw = k > 0, he = k + 2 < N;
+                    double yc[2], ys[2] = {0.0, 0.0}, yn[2] = {0.0, 0.0}, cw[2], cs[2], csn[2] = {0.0, 0.0}, bk[2];
+                    double yw = 0.0, ye = 0.0, cwe = 0.0;
+                    ld64<2>(y + k, yc);
+                    ld64<2>(cW64 + k, cw);
+                    ld64<2>(cS64 + k, cs);
+                    ld64<2>(bh + k, bk);
+                    if (hw) yw = __ldcg(y + k - 1);
+                    if (he) {
+                        ye = __ldcg(y + k + 2);
+                        cwe = cW64[k + 2];
+                    }
+                    if (hs) ld64<2>(y + k - nx, ys);
+                    if (hn) {
+                        ld64<2>(y + k + nx, yn);
+                        ld64<2>(cS64 + k + nx, csn);
+                    }
+                    float f[2];
+#pragma unroll
+                    for (int i = 0; i < 2; i++) {
+                        const double left = i == 0 ? yw : yc[0];
+                        const double right = i == 1 ? ye : yc[1];
+                        const double cright = i == 1 ? cwe : cw[1];
+                        const double rk = bk[i] - (yc[i] - cw[i] * left - cright * right - cs[i] * ys[i] - csn[i] * yn[i]);
+                        f[i] = static_cast<float>(rk * zs);
+                        rrf += f[i] * f[i];
+                        cr[1] = nanmax(cr[1], abs_ratio_approx(rk, yc[i]));
+                    }
+                    stf<2>(r0 + k, f);
+                }
+                cr[0] = static_cast<double>(rrf);
+                if (!allreduce<1, 1>(cr, w.partials, parity, w.bar, P.spin_limit, abort_flag, sh, team)) {
+                    timed_out = true;
+                    return false;
+                }
+                tr[0] = cr[0] / (scale * scale);
+                tr[3] = cr[1];
             }
             nref++;
             crit = tr[3];
-            l2 = sqrt(tr[1] / bb);
             if (!isfinite(tr[0]) || !(crit == crit)) {
                 status = kErrNonfinite;
                 return false;
@@ -562,10 +687,6 @@ __device__ bool tiled_solve(const SolveParams& P, const Workspace& w, RedShared&
             }
             rr = rr_true;
             rr_ref = rr_true;
-            if (!refresh(false)) {
-                timed_out = true;
-                return false;
-            }
             return true;
         };
 
@@ -602,6 +723,7 @@ __device__ bool tiled_solve(const SolveParams& P, const Workspace& w, RedShared&
                 float* __restrict__ pnew = pb[cur ^ 1];
                 const float rb = static_cast<float>(beta);
                 double v1[1] = {0.0};
+                float pqf = 0.f;      // this thread's p.q in FP32 (see down_pass)
                 for (int c = tid; c < nchunk; c += stride) {
                     const int k = c * 4;
                     const bool hs = k >= nx, hn = k + nx < N, hw = k > 0, he = k + 4 < N;
@@ -641,11 +763,12 @@ __device__ bool tiled_solve(const SolveParams& P, const Workspace& w, RedShared&
                         const float right = i == 3 ? pE : p[i + 1];
                         const float cright = i == 3 ? cwe : cw[i + 1];
                         qv[i] = p[i] - cw[i] * left - cright * right - cs[i] * pS[i] - csn[i] * pN[i];
-                        v1[0] += static_cast<double>(p[i]) * static_cast<double>(qv[i]);
+                        pqf += p[i] * qv[i];
                     }
                     stf<4>(pnew + k, p);
                     stf<4>(q + k, qv);
                 }
+                v1[0] = static_cast<double>(pqf);
                 if (!allreduce<1, 0>(v1, w.partials, parity, w.bar, P.spin_limit, abort_flag, sh, team)) {
                     timed_out = true;
                     break;
@@ -689,6 +812,42 @@ __device__ bool tiled_solve(const SolveParams& P, const Workspace& w, RedShared&
             }
             cyc_mark(msh.amg, team, kAmgMaxLevels - 2);
             if (!refine()) break;
+        }
+        // the paper's 2-norm |b - A x|_2 / |b|_2 of the final iterate (reported), once
+        if (!timed_out && nref > 0 && (status == kOk || status == kErrNotConverged)) {
+            double v[1] = {0.0};
+            for (int c = tid; c < N / 2; c += stride) {
+                const int k = c * 2;
+                const bool hs = k >= nx, hn = k + nx < N, hw = k > 0, he = k + 2 < N;
+                double yc[2], ys[2] = {0.0, 0.0}, yn[2] = {0.0, 0.0}, cw[2], cs[2], csn[2] = {0.0, 0.0}, bk[2], sk[2];
+                double yw = 0.0, ye = 0.0, cwe = 0.0;
+                ld64<2>(y + k, yc);
+                ld64<2>(cW64 + k, cw);
+                ld64<2>(cS64 + k, cs);
+                ld64<2>(bh + k, bk);
+                ld64<2>(s + k, sk);
+                if (hw) yw = __ldcg(y + k - 1);
+                if (he) {
+                    ye = __ldcg(y + k + 2);
+                    cwe = cW64[k + 2];
+                }
+                if (hs) ld64<2>(y + k - nx, ys);
+                if (hn) {
+                    ld64<2>(y + k + nx, yn);
+                    ld64<2>(cS64 + k + nx, csn);
+                }
+#pragma unroll
+                for (int i = 0; i < 2; i++) {
+                    const double left = i == 0 ? yw : yc[0];
+                    const double right = i == 1 ? ye : yc[1];
+                    const double cright = i == 1 ? cwe : cw[1];
+                    const double rk = bk[i] - (yc[i] - cw[i] * left - cright * right - cs[i] * ys[i] - csn[i] * yn[i]);
+                    const double ru = abs_ratio_approx(rk, sk[i]);
+                    v[0] += ru * ru;
+                }
+            }
+            if (!allreduce<1, 0>(v, w.partials, parity, w.bar, P.spin_limit, abort_flag, sh, team)) timed_out = true;
+            else l2 = sqrt(v[0] / bb);
         }
     }
 
