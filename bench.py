@@ -91,6 +91,8 @@ def parse():
                     help="0 Jacobi, 1 aggregation multigrid, 2 algebraic multigrid (default: per workload)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison path")
     ap.add_argument("--untiled", action="store_true", help="use the untiled solve kernel (comparison)")
+    ap.add_argument("--block-cells", type=int, default=0,
+                    help="multigrid levels of at most this many cells run in one block (0: library default)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
@@ -307,7 +309,7 @@ def run_ours(args):
         return info
 
     opts = F.SolverOptions(prec=prec, limiter=P.limiter, rtol=rtol, timing=1, precond=args.precond,
-                           untiled=int(args.untiled))
+                           untiled=int(args.untiled), mg_block_cells=args.block_cells)
     # accuracy reference: FP64 path solved tightly (untimed)
     ref_opts = F.SolverOptions(prec=0, limiter=P.limiter, rtol=1e-13, timing=0, max_iter=1000000)
     ref_info = one(ref_opts, check=False)       # may stop at the FP64 floor (status 4)

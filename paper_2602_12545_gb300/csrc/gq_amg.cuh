@@ -1031,6 +1031,7 @@ __device__ void amg0_v(const AV& L, const float* in, float* out, float om, Range
                        double* rzo) {
     const int nx = L.nx, N = L.n, nch = N >> 2;
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float rzf = 0.f, rzof = 0.f;   // this thread's partial sums in FP32 (FP64 per cell is slow on this part)
     for (int ch = rg.start; ch < nch; ch += rg.step) {
         const int k = ch << 2;
         const float4 v = __ldcg(reinterpret_cast<const float4*>(in + k));
@@ -1062,10 +1063,14 @@ __device__ void amg0_v(const AV& L, const float* in, float* out, float om, Range
             const float zz[4] = {zo.x, zo.y, zo.z, zo.w};
 #pragma unroll
             for (int j = 0; j < 4; j++) {
-                *rz += (double)bb[j] * (double)o[j];
-                *rzo += (double)bb[j] * (double)zz[j];
+                rzf += bb[j] * o[j];
+                rzof += bb[j] * zz[j];
             }
         }
+    }
+    if (MODE == 2 && rz) {
+        *rz += static_cast<double>(rzf);
+        *rzo += static_cast<double>(rzof);
     }
 }
 
@@ -1073,14 +1078,19 @@ __device__ void amg0_v(const AV& L, const float* in, float* out, float om, Range
 template <bool CG, bool BCG>
 __device__ void amg_sweep(const AV& L, const float* in, float* out, float om, Range rg, const float* zold,
                           double* rz, double* rzo) {
+    float rzf = 0.f, rzof = 0.f;   // this thread's partial sums in FP32
     for (int i = rg.start; i < L.n; i += rg.step) {
         const float vi = ldvec<CG>(in + i), bi = ldvec<BCG>(L.b + i);
         const float v = vi + om * (bi - amg_apply<CG>(L, in, i, vi));
         out[i] = v;
         if (rz) {
-            *rz += (double)bi * (double)v;
-            *rzo += (double)bi * (double)__ldcg(zold + i);
+            rzf += bi * v;
+            rzof += bi * __ldcg(zold + i);
         }
+    }
+    if (rz) {
+        *rz += static_cast<double>(rzf);
+        *rzo += static_cast<double>(rzof);
     }
 }
 

@@ -243,7 +243,9 @@ int solve_max_blocks_per_sm();
 // the tiled solve (gq_pcg_tiled.cu): its kernel, dynamic shared memory and eligibility
 const void* solve_kernel_tiled();
 size_t tiled_smem_bytes();
+int tiled_threads();
 bool tiled_eligible(const SolveParams& p, const Workspace& w);
+cudaError_t launch_tiled(const SolveParams& p, const Workspace& w, int grid, cudaStream_t st);
 int batch_solve_max_blocks_per_sm();
 cudaError_t launch_batch_setup(const BatchArgs& a, int total_setup_blocks, cudaStream_t st);
 cudaError_t launch_batch_solve(const BatchArgs& a, int grid, cudaStream_t st);

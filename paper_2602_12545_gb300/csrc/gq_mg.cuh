@@ -313,6 +313,7 @@ __device__ void cyc_postsmooth(const Lv& L, float om, Range rg, const float* zol
     const float* __restrict__ cS = L.cS;
     float* __restrict__ out = L.out;
     const int nx = L.nx, N = L.N;
+    float rzf = 0.f, rzof = 0.f;   // this thread's partial sums in FP32 (FP64 per cell is slow on this part)
 #pragma unroll 4
     for (int k = rg.start; k < N; k += rg.step) {
         const bool he = k + 1 < N, hn = k + nx < N;
@@ -325,9 +326,13 @@ __device__ void cyc_postsmooth(const Lv& L, float om, Range rg, const float* zol
         const float z = xc + om * (rk - ax);
         out[k] = z;
         if (rz) {
-            *rz += static_cast<double>(rk) * z;
-            *rzo += static_cast<double>(rk) * __ldcg(zold + k);
+            rzf += rk * z;
+            rzof += rk * __ldcg(zold + k);
         }
+    }
+    if (rz) {
+        *rz += static_cast<double>(rzf);
+        *rzo += static_cast<double>(rzof);
     }
 }
 
@@ -413,6 +418,7 @@ __device__ void cyc0_presmooth_v(const Lv& L, float om, Range rg) {
 __device__ void cyc0_update_presmooth_v(const Lv& L, const float* rold, float* rnew, const float* q, const float* p,
                                         float* d, float alpha, float om, Range rg, double* rr) {
     const int nx = L.nx, N = L.N, nchunk = N / 4;
+    float rrf = 0.f;               // this thread's partial sum in FP32
     for (int ch = rg.start; ch < nchunk; ch += rg.step) {
         const int k = 4 * ch;
         F4 c, s, n, qc, qs, qn;
@@ -435,16 +441,18 @@ __device__ void cyc0_update_presmooth_v(const Lv& L, const float* rold, float* r
         for (int i = 0; i < 4; i++) {
             x.v[i] = om * (2.f * c.v[i] - om * a.v[i]);
             dk.v[i] = dk.v[i] + alpha * pk.v[i];
-            *rr += static_cast<double>(c.v[i]) * static_cast<double>(c.v[i]);
+            rrf += c.v[i] * c.v[i];
         }
         st4(L.xa + k, x);
         st4(rnew + k, c);
         st4(d + k, dk);
     }
+    *rr += static_cast<double>(rrf);
 }
 
 __device__ void cyc0_postsmooth_v(const Lv& L, float om, Range rg, const float* zold, double* rz, double* rzo) {
     const int nx = L.nx, N = L.N, nchunk = N / 4;
+    float rzf = 0.f, rzof = 0.f;   // this thread's partial sums in FP32
     for (int q = rg.start; q < nchunk; q += rg.step) {
         const int k = 4 * q;
         F4 c, s, n;
@@ -457,11 +465,13 @@ __device__ void cyc0_postsmooth_v(const Lv& L, float om, Range rg, const float* 
 #pragma unroll
         for (int i = 0; i < 4; i++) {
             z.v[i] = c.v[i] + om * (rr.v[i] - a.v[i]);
-            *rz += static_cast<double>(rr.v[i]) * z.v[i];
-            *rzo += static_cast<double>(rr.v[i]) * zo.v[i];
+            rzf += rr.v[i] * z.v[i];
+            rzof += rr.v[i] * zo.v[i];
         }
         st4(L.out + k, z);
     }
+    *rz += static_cast<double>(rzf);
+    *rzo += static_cast<double>(rzof);
 }
 
 // prolongation + one sweep on 4 fine cells of one row; parents of the chunk are the coarse

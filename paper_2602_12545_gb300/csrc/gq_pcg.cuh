@@ -52,7 +52,7 @@ constexpr int kStallChecks = 6;      // ... within this many consecutive checks
 constexpr int kStallIters = 32;      // ... spanning at least this many Krylov iterations
 
 struct RedShared {
-    double warp[kSolveThreads / 32][kSlots];
+    double warp[32][kSlots];           // up to 1024 threads a block
     double tot[kSlots];
 };
 
@@ -488,6 +488,7 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
                 const R rb = static_cast<R>(beta);
                 const R rsc = static_cast<R>(scale);
                 double v1[1] = {0.0};
+                R pqr = R(0);     // mixed path: this thread's p.q in FP32 (FP64 per cell is slow on this part)
                 for (int c = tid; c < nchunk; c += stride) {
                     const int k = c * W;
                     const bool hs = k >= nx, hn = k + nx < N, hw = k > 0, he = k + W < N;
@@ -568,7 +569,7 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
                         const R right = i == W - 1 ? pE : p[i + 1];
                         const R cright = i == W - 1 ? cwe : cw[i + 1];
                         qv[i] = p[i] - cw[i] * left - cright * right - cs[i] * pS[i] - csn[i] * pN[i];
-                        v1[0] += static_cast<double>(p[i]) * static_cast<double>(qv[i]);
+                        pqr += p[i] * qv[i];
                     }
                     stv<R, W>(pnew + k, p);
                     stv<R, W>(q + k, qv);
@@ -580,6 +581,7 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
                         stv<R, W>(d + k, zero);
                     }
                 }
+                v1[0] = static_cast<double>(pqr);
                 if (!allreduce<1, 0>(v1, w.partials, parity, w.bar, P.spin_limit, abort_flag, sh, team)) {
                     timed_out = true;
                     break;
@@ -619,6 +621,7 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
                             fused = true;
                         }
                     }
+                    R rrr = R(0);     // mixed path: this thread's r.r in FP32
                     for (int c = fused ? nchunk : tid; c < nchunk; c += stride) {
                         const int k = c * W;
                         R pk[W], qk[W], rk[W], xk[W];
@@ -630,7 +633,7 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
                         for (int i = 0; i < W; i++) {
                             rk[i] = rk[i] - ra * qk[i];
                             xk[i] = xk[i] + ra * pk[i];
-                            v2[0] += static_cast<double>(rk[i]) * static_cast<double>(rk[i]);
+                            rrr += rk[i] * rk[i];
                             // recursive stop estimate in FP32 (FP64 division is slow on this part;
                             // the decisive test uses the exact FP64 residual)
                             if constexpr (!MIXED)
@@ -645,6 +648,7 @@ __device__ __forceinline__ bool pcg_solve_w(const SolveParams& P, const Workspac
                             stf<W>(r0 + k, f);
                         }
                     }
+                    v2[0] += static_cast<double>(rrr);
                     if (!allreduce<1, 1>(v2, w.partials, parity, w.bar, P.spin_limit, abort_flag, sh, team)) {
                         timed_out = true;
                         break;

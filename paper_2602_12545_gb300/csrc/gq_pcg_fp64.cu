@@ -27,7 +27,7 @@ int solve_max_blocks_per_sm() {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, solve_kernel_fp64(), kSolveThreads, 0);
     int m = a < b ? a : b;
     if (cudaGetDevice(&dev) == cudaSuccess && tiled_ready(dev) &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, solve_kernel_tiled(), kSolveThreads, tiled_smem_bytes()) ==
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, solve_kernel_tiled(), tiled_threads(), tiled_smem_bytes()) ==
             cudaSuccess &&
         c >= 1)
         m = m < c ? m : c;
@@ -42,9 +42,12 @@ cudaError_t launch_solve(const SolveParams& p, const Workspace& w, int grid, cud
     int dev = 0;
     if (kernel) *kernel = 0;
     if (p.tiled && tiled_eligible(p, w) && cudaGetDevice(&dev) == cudaSuccess && tiled_ready(dev)) {
-        if (kernel) *kernel = 1;
-        return cudaLaunchCooperativeKernel(solve_kernel_tiled(), dim3(grid), dim3(kSolveThreads), args,
-                                           tiled_smem_bytes(), st);
+        const cudaError_t e = launch_tiled(p, w, grid, st);
+        if (e != cudaErrorInvalidValue) {
+            if (kernel) *kernel = 1;
+            return e;
+        }
+        cudaGetLastError();     // the tensor maps could not be built: the untiled kernel
     }
     const void* fn = p.mixed ? solve_kernel_mixed() : solve_kernel_fp64();
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kSolveThreads), args, 0, st);

@@ -27,11 +27,17 @@
 // Used for the mixed path with the aggregation preconditioner when every level the
 // whole grid works on has a width divisible by 8 and an even height (16-byte staging
 // chunks on the level and on its parent); other problems use k_pcg.
+#include <cuda.h>
+
+#include <cstring>
+#include <mutex>
+
 #include "gq_pcg.cuh"
 
 namespace gq {
 namespace {
 
+constexpr int kTiledThreads = 512;     // threads of a block (1024 measured slower: 64 registers, spills, costlier barriers)
 constexpr int kTX = 64, kTY = 16;      // tile of a level (cells)
 constexpr int kHX = 4, kHY = 2;        // staged halo: x one 16-byte chunk, y two rows
 constexpr int kRW = kTX + 2 * kHX;     // staged region width (72)
@@ -66,28 +72,61 @@ struct TileSmem {
 };
 static_assert(3 * kBlkCap <= kNst * kStaged * kNR, "block-level vectors must fit the staging buffers");
 
-__device__ __forceinline__ void cp16(float* dst, const float* src, bool ok) {
-    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 16 : 0) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
+// ---- TMA staging ---------------------------------------------------------------------
+// Every staged array of a level has a tensor map (2-D, FP32, the level's nx x ny with a
+// row stride of 4 nx bytes) whose box is the region a tile needs: kRW x kRH with a halo,
+// kCW x kCH over the parent level, or kTX x kTY for the tile alone.  Box origins are
+// multiples of 4 cells in x (16 bytes), as the tensor copy requires; rows and columns
+// outside the grid are filled with zeros.  One thread issues a tile's copies after
+// announcing their bytes on the stage's mbarrier; every thread waits on the barrier's
+// phase, with a bounded number of polls.
+constexpr int kMaxTiledLevels = 12;
+constexpr int kMapsPerLevel = 8;
+enum { kMapR0 = 0, kMapR1, kMapCW, kMapCS, kMapT, kMapXA, kMapXC, kMapQ };
+constexpr int kOwnBase = kMaxTiledLevels * kMapsPerLevel;
+enum { kOwnP0 = 0, kOwnP1, kOwnD, kOwnZ, kOwnZold, kOwnCount };
+constexpr int kNumMaps = kOwnBase + kOwnCount;
+constexpr unsigned kHaloBytes = kNR * 4, kCoarseBytes = kNC * 4, kOwnBytes = kNT * 4;
 
-// stage the region of g (nx x ny, nx % 4 == 0) with origin (X0, Y0), X0 % 4 == 0, size
-// RW x RH (RW % 4 == 0) into dst; chunks outside the grid are zero-filled
-template <int RW, int RH>
-__device__ __forceinline__ void stage(float* dst, const float* g, int nx, int ny, int X0, int Y0) {
-    constexpr int CPR = RW / 4;
-    for (int c = threadIdx.x; c < CPR * RH; c += blockDim.x) {
-        const int row = c / CPR, col = c - row * CPR;
-        const int gx = X0 + 4 * col, gy = Y0 + row;
-        const bool ok = gy >= 0 && gy < ny && gx >= 0 && gx < nx;
-        cp16(dst + row * RW + 4 * col, ok ? g + (size_t)gy * nx + gx : g, ok);
-    }
+struct TiledMaps {
+    CUtensorMap m[kNumMaps];
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return static_cast<unsigned>(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(b)), "r"(count) : "memory");
 }
+__device__ __forceinline__ void mbar_expect(unsigned long long* b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned long long* b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void tma2d(void* dst, const CUtensorMap* map, int x, int y, unsigned long long* b) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_u32(b))
+        : "memory");
+}
+// orders this thread's view of memory (generic stores of other blocks acquired at the last grid
+// barrier, generic reads of a buffer before the copies that overwrite it) before its next
+// tensor copies
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;\n" ::: "memory"); }
+
+// The mbarriers of the staging buffers and the phase each is in (identical in every thread).
+struct TilePipe {
+    unsigned long long* bar;   // [kNst] in shared memory
+    unsigned phase;            // bit k: parity of the phase buffer k completes next
+    long long spin;            // poll limit of a wait
+};
 
 // (A v) at region index i: unit diagonal, couplings staged like v
 __device__ __forceinline__ float st5(const float* v, const float* cw, const float* cs, int i) {
@@ -96,6 +135,7 @@ __device__ __forceinline__ float st5(const float* v, const float* cw, const floa
 
 struct TLevel {
     int nx, ny;                // cells (nx % 8 == 0, ny even)
+    int mr, mcw, mcs, mt, mxa, mxc;   // tensor maps of r, cW, cS, t, x_a and the parent's result
     const float* cW;
     const float* cS;
     const float* t;            // transfer weight to the parent
@@ -117,34 +157,50 @@ __device__ __forceinline__ void tile_origin(const TLevel& L, int t, int& x0, int
 }
 
 // The tiles b, b + G, b + 2G, ... of a pass, each staged kNst - 1 tiles ahead of its
-// arithmetic: issue(t, buf) enqueues tile t's copies into buffer buf, compute(t, buf)
-// works on it.  One commit group per tile (empty ones included), so that waiting for
-// all but the newest kNst - 1 groups means the oldest tile has landed.
+// arithmetic: issue(t, buf) (thread 0) starts tile t's copies into buffer buf,
+// compute(t, buf) works on it.  Returns false when a wait ran out of polls (the pass's
+// copies still in flight are then waited for, again with a bound).
 template <class Issue, class Compute>
-__device__ __forceinline__ void tile_loop(int nt, int b, int G, Issue issue, Compute compute) {
+__device__ __forceinline__ bool tile_loop(int nt, int b, int G, TilePipe& pp, Issue issue, Compute compute) {
+    if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < kNst - 1; k++) {
-        const int t = b + k * G;
-        if (t < nt) issue(t, k);
-        cp_commit();
+        for (int k = 0; k < kNst - 1; k++) {
+            const int t = b + k * G;
+            if (t < nt) issue(t, k);
+        }
     }
     int i = 0;
     for (int t = b; t < nt; t += G, i++) {
+        const int buf = i % kNst;
         const int tn = t + (kNst - 1) * G;
-        if (tn < nt) issue(tn, (i + kNst - 1) % kNst);
-        cp_commit();
-        cp_wait<kNst - 1>();
-        __syncthreads();
-        compute(t, i % kNst);
+        if (threadIdx.x == 0 && tn < nt) issue(tn, (i + kNst - 1) % kNst);
+        const unsigned par = (pp.phase >> buf) & 1u;
+        bool done = mbar_try(&pp.bar[buf], par);
+        for (long long n = 0; !done && n < pp.spin; n++) done = mbar_try(&pp.bar[buf], par);
+        pp.phase ^= 1u << buf;
+        if (__syncthreads_or(!done)) {
+            // drain: the tiles issued after this one (bounded waits)
+            for (int j = 1; j < kNst; j++) {
+                if (t + j * G >= nt) break;
+                const int bj = (i + j) % kNst;
+                const unsigned pj = (pp.phase >> bj) & 1u;
+                bool dj = mbar_try(&pp.bar[bj], pj);
+                for (long long n = 0; !dj && n < pp.spin; n++) dj = mbar_try(&pp.bar[bj], pj);
+                pp.phase ^= 1u << bj;
+            }
+            return false;
+        }
+        compute(t, buf);
         __syncthreads();
     }
-    cp_wait<0>();
+    return true;
 }
 
 // Kernel-wide arguments of the fused level-0 down pass: the Krylov update.
 struct UpdateArgs {
     bool on;                   // false: plain down pass on r
     float alpha;
+    int mq, mp, md;            // tensor maps of q, p and d
     const float* q;            // q = A p
     const float* p;            // the direction
     float* d;                  // correction (updated in place)
@@ -154,22 +210,27 @@ struct UpdateArgs {
 // Down pass of one level over all of its tiles this block owns (tiles b, b + G, ...).
 // Staged with a halo: 0 r (or r_old), 1 q (update only), 2 cW, 3 cS, 4 t; the tile
 // alone: 0 p, 1 d (update only).
-__device__ void down_pass(const TLevel& L, float om, const UpdateArgs& U, TileSmem& S, int b, int G, double* rr) {
+__device__ bool down_pass(const TLevel& L, float om, const UpdateArgs& U, TileSmem& S, const TiledMaps& M, TilePipe& pp,
+                          int b, int G, double* rr) {
     // this thread's r'.r' over its cells of the pass, in FP32 (a few dozen terms; FP64
     // arithmetic per cell would cost more than the pass's memory traffic on this part)
     float rrf = 0.f;
+    const unsigned bytes = 4 * kHaloBytes + (U.on ? kHaloBytes + 2 * kOwnBytes : 0u);
     auto issue = [&](int t, int buf) {
         int x0, y0;
         tile_origin(L, t, x0, y0);
         const int X0 = x0 - kHX, Y0 = y0 - kHY;
-        stage<kRW, kRH>(S.in[buf][0], L.r, L.nx, L.ny, X0, Y0);
-        stage<kRW, kRH>(S.in[buf][2], L.cW, L.nx, L.ny, X0, Y0);
-        stage<kRW, kRH>(S.in[buf][3], L.cS, L.nx, L.ny, X0, Y0);
-        stage<kRW, kRH>(S.in[buf][4], L.t, L.nx, L.ny, X0, Y0);
+        unsigned long long* bar = &pp.bar[buf];
+        fence_proxy_async();
+        mbar_expect(bar, bytes);
+        tma2d(S.in[buf][0], &M.m[L.mr], X0, Y0, bar);
+        tma2d(S.in[buf][2], &M.m[L.mcw], X0, Y0, bar);
+        tma2d(S.in[buf][3], &M.m[L.mcs], X0, Y0, bar);
+        tma2d(S.in[buf][4], &M.m[L.mt], X0, Y0, bar);
         if (U.on) {
-            stage<kRW, kRH>(S.in[buf][1], U.q, L.nx, L.ny, X0, Y0);
-            stage<kTX, kTY>(S.own[buf][0], U.p, L.nx, L.ny, x0, y0);
-            stage<kTX, kTY>(S.own[buf][1], U.d, L.nx, L.ny, x0, y0);
+            tma2d(S.in[buf][1], &M.m[U.mq], X0, Y0, bar);
+            tma2d(S.own[buf][0], &M.m[U.mp], x0, y0, bar);
+            tma2d(S.own[buf][1], &M.m[U.md], x0, y0, bar);
         }
     };
     auto compute = [&](int t, int buf) {
@@ -225,27 +286,33 @@ __device__ void down_pass(const TLevel& L, float om, const UpdateArgs& U, TileSm
             }
         }
     };
-    tile_loop(ntiles(L), b, G, issue, compute);
+    const bool ok = tile_loop(ntiles(L), b, G, pp, issue, compute);
     *rr += static_cast<double>(rrf);
+    return ok;
 }
 
 // Up pass of one level.  Staged with a halo: 0 x_a, 1 t, 2 cW, 3 cS, 4 r; coarse: the
 // parent's result; the tile alone: 0 z_old (level 0).  Level 0 (zold != null): out is z,
 // with the partial sums r.z and r.z_old.
-__device__ void up_pass(const TLevel& L, float om, float over, TileSmem& S, int b, int G, const float* zold,
-                        double* rz, double* rzo) {
+__device__ bool up_pass(const TLevel& L, float om, float over, TileSmem& S, const TiledMaps& M, TilePipe& pp, int b,
+                        int G, int mzold, double* rz, double* rzo) {
     float rzf = 0.f, rzof = 0.f;       // this thread's partial sums (FP32, see down_pass)
+    const bool lvl0 = mzold >= 0;
+    const unsigned bytes = 5 * kHaloBytes + kCoarseBytes + (lvl0 ? kOwnBytes : 0u);
     auto issue = [&](int t, int buf) {
         int x0, y0;
         tile_origin(L, t, x0, y0);
         const int X0 = x0 - kHX, Y0 = y0 - kHY;
-        stage<kRW, kRH>(S.in[buf][0], L.xa, L.nx, L.ny, X0, Y0);
-        stage<kRW, kRH>(S.in[buf][1], L.t, L.nx, L.ny, X0, Y0);
-        stage<kRW, kRH>(S.in[buf][2], L.cW, L.nx, L.ny, X0, Y0);
-        stage<kRW, kRH>(S.in[buf][3], L.cS, L.nx, L.ny, X0, Y0);
-        stage<kRW, kRH>(S.in[buf][4], L.r, L.nx, L.ny, X0, Y0);
-        stage<kCW, kCH>(S.co[buf], L.xc, L.cnx, L.cny, x0 / 2 - 4, y0 / 2 - 2);
-        if (zold) stage<kTX, kTY>(S.own[buf][0], zold, L.nx, L.ny, x0, y0);
+        unsigned long long* bar = &pp.bar[buf];
+        fence_proxy_async();
+        mbar_expect(bar, bytes);
+        tma2d(S.in[buf][0], &M.m[L.mxa], X0, Y0, bar);
+        tma2d(S.in[buf][1], &M.m[L.mt], X0, Y0, bar);
+        tma2d(S.in[buf][2], &M.m[L.mcw], X0, Y0, bar);
+        tma2d(S.in[buf][3], &M.m[L.mcs], X0, Y0, bar);
+        tma2d(S.in[buf][4], &M.m[L.mr], X0, Y0, bar);
+        tma2d(S.co[buf], &M.m[L.mxc], x0 / 2 - 4, y0 / 2 - 2, bar);
+        if (lvl0) tma2d(S.own[buf][0], &M.m[mzold], x0, y0, bar);
     };
     auto compute = [&](int t, int buf) {
         int x0, y0;
@@ -285,17 +352,18 @@ __device__ void up_pass(const TLevel& L, float om, float over, TileSmem& S, int 
             const int ix = (kHY + ly) * kRW + (kHX + lx);
             const float o = XB[ix] + om * (R[ix] - st5(XB, CW, CS, ix));
             L.out[(size_t)gy * L.nx + gx] = o;
-            if (zold) {
+            if (lvl0) {
                 rzf += R[ix] * o;
                 rzof += R[ix] * S.own[buf][0][e];
             }
         }
     };
-    tile_loop(ntiles(L), b, G, issue, compute);
-    if (zold) {
+    const bool ok = tile_loop(ntiles(L), b, G, pp, issue, compute);
+    if (lvl0) {
         *rz += static_cast<double>(rzf);
         *rzo += static_cast<double>(rzof);
     }
+    return ok;
 }
 
 }  // namespace
@@ -306,7 +374,8 @@ namespace {
 
 // The solve of k_pcg<true> with the aggregation V-cycle (gq_pcg.cuh, pcg_solve_w), its
 // team levels run by the tiled passes above.  Returns false when a wait timed out.
-__device__ bool tiled_solve(const SolveParams& P, const Workspace& w, RedShared& sh, MGShared& msh, TileSmem& S) {
+__device__ bool tiled_solve(const SolveParams& P, const Workspace& w, RedShared& sh, MGShared& msh, TileSmem& S,
+                            const TiledMaps& TM, TilePipe& pp) {
     const Team team{static_cast<int>(blockIdx.x), static_cast<int>(gridDim.x)};
     const int N = P.N, nx = P.nx;
     const int nchunk = N / 4;
@@ -329,6 +398,7 @@ __device__ bool tiled_solve(const SolveParams& P, const Workspace& w, RedShared&
     float* rbuf[2] = {w.r32, w.r32b};
     int rsel = 0;
     float* zc = w.mg.z;
+    int zsel = 0;                        // 0: zc is mg.z and zo mg.zold; 1: swapped
     float* zo = w.mg.zold;
     const MGHierarchy& mg = w.mg;
 
@@ -357,6 +427,13 @@ __device__ bool tiled_solve(const SolveParams& P, const Workspace& w, RedShared&
         TLevel t;
         t.nx = M.nx;
         t.ny = M.ny;
+        const int base = l * kMapsPerLevel;
+        t.mr = base + (l == 0 ? kMapR0 + rsel : kMapR0);
+        t.mcw = base + kMapCW;
+        t.mcs = base + kMapCS;
+        t.mt = base + kMapT;
+        t.mxa = base + kMapXA;
+        t.mxc = base + kMapXC;
         t.cW = M.cW;
         t.cS = M.cS;
         t.t = M.t;
@@ -392,7 +469,7 @@ __device__ bool tiled_solve(const SolveParams& P, const Workspace& w, RedShared&
         for (int e = threadIdx.x; e < nc * nc; e += blockDim.x) S.blk.inv[e] = __ldcg(mg.inv + e);
         __syncthreads();
     }
-    const UpdateArgs no_update{false, 0.f, nullptr, nullptr, nullptr, nullptr};
+    const UpdateArgs no_update{false, 0.f, 0, 0, 0, nullptr, nullptr, nullptr, nullptr};
 
     // V-cycle z = B r: down passes (level 0's may be done, fused with the update), the
     // block levels, up passes; rz, rzo receive this thread's r.z and r.z_old
@@ -400,7 +477,7 @@ __device__ bool tiled_solve(const SolveParams& P, const Workspace& w, RedShared&
         for (int l = pre0_done ? 1 : 0; l < lg; l++) {
             cyc_mark(msh.amg, team, l);
             double unused = 0.0;
-            down_pass(tlevel(l), om, no_update, S, team.rank, team.size, &unused);
+            if (!down_pass(tlevel(l), om, no_update, S, TM, pp, team.rank, team.size, &unused)) return false;
             if (!bar()) return false;
         }
         if (team.rank == 0 && blk_smem) {
@@ -477,11 +554,13 @@ __device__ bool tiled_solve(const SolveParams& P, const Workspace& w, RedShared&
         if (!bar()) return false;
         for (int l = lg - 1; l >= 1; l--) {
             cyc_mark(msh.amg, team, l);
-            up_pass(tlevel(l), om, over, S, team.rank, team.size, nullptr, nullptr, nullptr);
+            if (!up_pass(tlevel(l), om, over, S, TM, pp, team.rank, team.size, -1, nullptr, nullptr)) return false;
             if (!bar()) return false;
         }
         cyc_mark(msh.amg, team, 0);
-        up_pass(tlevel(0), om, over, S, team.rank, team.size, zo, rz, rzo);
+        if (!up_pass(tlevel(0), om, over, S, TM, pp, team.rank, team.size, kOwnBase + (zsel ? kOwnZ : kOwnZold), rz,
+                     rzo))
+            return false;
         cyc_mark(msh.amg, team, kAmgMaxLevels - 1);
         return true;
     };
@@ -783,14 +862,21 @@ __device__ bool tiled_solve(const SolveParams& P, const Workspace& w, RedShared&
                     const double alpha = rho_mg / pq;
                     float* tz = zc;          // this z becomes z_old of the next cycle
                     zc = zo;
+                    zsel ^= 1;
                     zo = tz;
                     cur ^= 1;
                     // ---- U fused with the next cycle's level-0 down pass ---------------------
                     cyc_mark(msh.amg, team, kAmgMaxLevels - 3);
                     double v2[2] = {0.0, 0.0};
-                    const UpdateArgs upd{true, static_cast<float>(alpha), q, pnew, d, rbuf[rsel ^ 1]};
-                    down_pass(tlevel(0), om, upd, S, team.rank, team.size, &v2[0]);
+                    // pnew is pb[cur] now (cur was flipped above)
+                    const UpdateArgs upd{true, static_cast<float>(alpha), kMapQ, kOwnBase + kOwnP0 + cur,
+                                         kOwnBase + kOwnD, q, pnew, d, rbuf[rsel ^ 1]};
+                    const bool okp = down_pass(tlevel(0), om, upd, S, TM, pp, team.rank, team.size, &v2[0]);
                     rsel ^= 1;
+                    if (!okp) {
+                        timed_out = true;
+                        break;
+                    }
                     if (!allreduce<1, 1>(v2, w.partials, parity, w.bar, P.spin_limit, abort_flag, sh, team)) {
                         timed_out = true;
                         break;
@@ -868,17 +954,112 @@ done:
     return true;
 }
 
-__global__ void __launch_bounds__(kSolveThreads, 1) k_pcg_tiled(SolveParams P, Workspace w) {
+__global__ void __launch_bounds__(kTiledThreads, 1) k_pcg_tiled(SolveParams P, Workspace w,
+                                                                const __grid_constant__ TiledMaps TM) {
     __shared__ RedShared sh;
     __shared__ MGShared msh;
-    extern __shared__ __align__(16) unsigned char tile_raw[];
-    TileSmem& S = *reinterpret_cast<TileSmem*>(tile_raw);
-    tiled_solve(P, w, sh, msh, S);
+    __shared__ unsigned long long tile_bar[kNst];
+    extern __shared__ __align__(128) unsigned char tile_raw[];
+    // tensor copies land on 128-byte aligned buffers
+    const unsigned pad = (128u - (smem_u32(tile_raw) & 127u)) & 127u;
+    TileSmem& S = *reinterpret_cast<TileSmem*>(tile_raw + pad);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < kNst; k++) mbar_init(&tile_bar[k], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        fence_proxy_async();
+    }
+    __syncthreads();
+    TilePipe pp{tile_bar, 0u, P.spin_limit};
+    tiled_solve(P, w, sh, msh, S, TM, pp);
 }
 
 }  // namespace
 
-size_t tiled_smem_bytes() { return sizeof(TileSmem); }
+size_t tiled_smem_bytes() { return sizeof(TileSmem) + 128; }
+
+int tiled_threads() { return kTiledThreads; }
+
+namespace {
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_fn() {
+    static EncodeTiled fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// 2-D FP32 tensor map of an nx x ny row-major array (nx % 4 == 0) with box bw x bh
+bool encode(CUtensorMap* m, const float* base, int nx, int ny, int bw, int bh) {
+    EncodeTiled fn = encode_fn();
+    if (!fn || !base || nx % 4 != 0 || (reinterpret_cast<uintptr_t>(base) & 15u) != 0) return false;
+    const cuuint64_t dims[2] = {static_cast<cuuint64_t>(nx), static_cast<cuuint64_t>(ny)};
+    const cuuint64_t strides[1] = {static_cast<cuuint64_t>(nx) * sizeof(float)};
+    const cuuint32_t box[2] = {static_cast<cuuint32_t>(bw), static_cast<cuuint32_t>(bh)};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+// the tensor maps of every array the tiled solve stages, laid out as the kernel indexes them
+bool build_tiled_maps(const SolveParams& p, const Workspace& w, TiledMaps* M) {
+    const MGHierarchy& mg = w.mg;
+    int lg = 0;
+    while (lg < mg.nlev - 1 && mg.L[lg].N > p.block_cells) lg++;
+    if (lg < 1 || lg > kMaxTiledLevels) return false;
+    std::memset(M, 0, sizeof(*M));
+    bool ok = true;
+    for (int l = 0; l < lg && ok; l++) {
+        const MGLevel& L = mg.L[l];
+        const MGLevel& C = mg.L[l + 1];
+        CUtensorMap* m = M->m + l * kMapsPerLevel;
+        const float* r0 = l == 0 ? w.r32 : L.r;
+        ok = ok && encode(&m[kMapR0], r0, L.nx, L.ny, kRW, kRH);
+        if (l == 0) ok = ok && encode(&m[kMapR1], w.r32b, L.nx, L.ny, kRW, kRH);
+        ok = ok && encode(&m[kMapCW], L.cW, L.nx, L.ny, kRW, kRH);
+        ok = ok && encode(&m[kMapCS], L.cS, L.nx, L.ny, kRW, kRH);
+        ok = ok && encode(&m[kMapT], L.t, L.nx, L.ny, kRW, kRH);
+        ok = ok && encode(&m[kMapXA], L.xa, L.nx, L.ny, kRW, kRH);
+        ok = ok && encode(&m[kMapXC], l + 1 == lg ? C.xa : C.xb, C.nx, C.ny, kCW, kCH);
+        if (l == 0) ok = ok && encode(&m[kMapQ], w.q32, L.nx, L.ny, kRW, kRH);
+    }
+    const MGLevel& L0 = mg.L[0];
+    CUtensorMap* o = M->m + kOwnBase;
+    ok = ok && encode(&o[kOwnP0], w.p32[0], L0.nx, L0.ny, kTX, kTY);
+    ok = ok && encode(&o[kOwnP1], w.p32[1], L0.nx, L0.ny, kTX, kTY);
+    ok = ok && encode(&o[kOwnD], w.d32, L0.nx, L0.ny, kTX, kTY);
+    ok = ok && encode(&o[kOwnZ], mg.z, L0.nx, L0.ny, kTX, kTY);
+    ok = ok && encode(&o[kOwnZold], mg.zold, L0.nx, L0.ny, kTX, kTY);
+    return ok;
+}
+
+cudaError_t launch_tiled(const SolveParams& p, const Workspace& w, int grid, cudaStream_t st) {
+    static TiledMaps maps;     // host staging of the kernel's parameter (copied at launch)
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!build_tiled_maps(p, w, &maps)) return cudaErrorInvalidValue;
+    SolveParams pc = p;
+    Workspace wc = w;
+    void* args[] = {&pc, &wc, &maps};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_pcg_tiled), dim3(grid), dim3(kTiledThreads),
+                                       args, tiled_smem_bytes(), st);
+}
 
 const void* solve_kernel_tiled() { return reinterpret_cast<const void*>(k_pcg_tiled); }
 
@@ -887,11 +1068,12 @@ const void* solve_kernel_tiled() { return reinterpret_cast<const void*>(k_pcg_ti
 bool tiled_eligible(const SolveParams& p, const Workspace& w) {
     if (!p.mixed || p.precond != GQ_PRECOND_MG || w.mg.nlev < 2) return false;
     if (p.N <= p.block_cells) return false;
-    for (int l = 0; l < w.mg.nlev - 1 && w.mg.L[l].N > p.block_cells; l++) {
+    int l = 0;
+    for (; l < w.mg.nlev - 1 && w.mg.L[l].N > p.block_cells; l++) {
         const MGLevel& L = w.mg.L[l];
         if (L.nx % 8 != 0 || L.ny % 2 != 0) return false;
     }
-    return true;
+    return l <= kMaxTiledLevels && encode_fn() != nullptr;
 }
 
 }  // namespace gq
