@@ -396,7 +396,8 @@ gq_status gq_fld_step_batched(gq_fld_plan *const *plans, int n, const gq_batch_i
  * number of consecutive implicit steps) are queued with host copies of their inputs.
  * Each engine tick (gq_server_poll) admits queued requests in arrival order while their
  * device footprint fits the memory budget, keeps admitted requests' state resident on
- * the device, steps every resident request once in one batched launch, and retires the
+ * the device, steps every resident request once (the smaller ones together in one
+ * batched launch, the large ones each on the whole GPU right after it), and retires the
  * finished ones (results copied to the caller's host buffers, memory returned).  Not in
  * the paper.
  * --------------------------------------------------------------------------------------- */
@@ -405,7 +406,11 @@ typedef struct {
     size_t budget_bytes;   /* device bytes resident requests may hold (plans + fields), > 0 */
     int max_active;        /* most requests resident and stepped together (0 = 256) */
     int use_graph;         /* 1: replay a captured graph while the resident set is unchanged */
-    int reserved[6];
+    int solo_cells;        /* requests of at least this many cells step alone on the whole GPU
+                              (gq_fld_step) after the batched launch of the smaller ones;
+                              0 = 524288 (the size at which a batch team reaches its cap);
+                              < 0: every request in the batched launch */
+    int reserved[5];
 } gq_server_opts;
 
 typedef struct {

@@ -101,7 +101,7 @@ class BatchOpts(ctypes.Structure):
 
 class ServerOpts(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_size_t), ("max_active", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("solo_cells", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
 class Request(ctypes.Structure):

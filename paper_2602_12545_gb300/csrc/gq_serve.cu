@@ -5,8 +5,11 @@
 //   1. admits queued requests in arrival order while their device footprint (plan
 //      arena plus rho, e_g, E_r, T_g) fits the memory budget and the active-set cap;
 //      admission builds the plan and uploads the fields, which then stay resident;
-//   2. steps every resident request once, all in one batched persistent launch, so work
-//      from requests that arrived at different times overlaps on the device;
+//   2. steps every resident request once: the smaller ones together in one batched
+//      persistent launch, so work from requests that arrived at different times overlaps
+//      on the device, then each request of at least solo_cells cells alone on the whole
+//      GPU (a batch team is capped at a few blocks, which would leave a large grid
+//      running on a fraction of the SMs while the small ones finish);
 //   3. retires requests that finished their steps (or failed): results are copied to the
 //      caller's host buffers and their device memory is returned to the budget.
 // The paper has no counterpart (its code advances one simulation per MPI job).
@@ -152,6 +155,7 @@ gq_status gq_server_create(const gq_server_opts* opts, gq_server** out) {
     if (!S) return GQ_ERR_OOM;
     S->opts = *opts;
     if (S->opts.max_active == 0) S->opts.max_active = 256;
+    if (S->opts.solo_cells == 0) S->opts.solo_cells = 1 << 19;
     if (cudaGetDevice(&S->device) != cudaSuccess) {
         delete S;
         return GQ_ERR_CUDA;
@@ -246,35 +250,48 @@ gq_status gq_server_poll(gq_server* S, int* completed) {
         if (completed) *completed = done;
         return GQ_OK;
     }
-    // 2. one step of every resident request, in one batched launch
+    // 2. one step of every resident request: the small ones in one batched launch, the
+    //    large ones (at least solo_cells cells) each alone on the whole GPU
     const int n = (int)S->active.size();
-    std::vector<gq_fld_plan*> plans(n);
-    for (int p = 0; p < n; p++) plans[p] = S->active[p]->plan;
-    if (plans != S->bound) {
-        gq_status st = gq::batch_rebind(S->batch, plans.data(), n);
-        if (st != GQ_OK) {
-            if (cur != S->device) cudaSetDevice(cur);
-            return st;
-        }
-        S->bound = plans;
-    }
-    S->items.assign(n, gq_batch_item{});
     S->infos.assign(n, gq_step_info{});
+    std::vector<int> small, large;
     for (int p = 0; p < n; p++) {
-        ServeReq* R = S->active[p];
-        const size_t N = (size_t)R->nx * R->ny;
-        gq_batch_item& it = S->items[p];
-        it.rho = R->dfields;
-        it.e_g = R->dfields + N;
-        it.E_r = R->dfields + 2 * N;
-        it.T_g_out = R->dfields + 3 * N;
-        it.opacity = R->op;
-        it.eos = R->eos;
-        it.dt = R->dt;
-        it.bc = R->bc;
-        it.opts = R->opts;
+        const ServeReq* R = S->active[p];
+        const long long cells = (long long)R->nx * R->ny;
+        (S->opts.solo_cells > 0 && cells >= S->opts.solo_cells ? large : small).push_back(p);
     }
-    gq_status bst = gq_batch_step(S->batch, S->items.data(), S->stream, S->infos.data());
+    gq_status bst = GQ_OK;
+    if (!small.empty()) {
+        const int m = (int)small.size();
+        std::vector<gq_fld_plan*> plans(m);
+        for (int i = 0; i < m; i++) plans[i] = S->active[small[i]]->plan;
+        if (plans != S->bound) {
+            gq_status st = gq::batch_rebind(S->batch, plans.data(), m);
+            if (st != GQ_OK) {
+                if (cur != S->device) cudaSetDevice(cur);
+                return st;
+            }
+            S->bound = plans;
+        }
+        S->items.assign(m, gq_batch_item{});
+        std::vector<gq_step_info> binfo(m);
+        for (int i = 0; i < m; i++) {
+            ServeReq* R = S->active[small[i]];
+            const size_t N = (size_t)R->nx * R->ny;
+            gq_batch_item& it = S->items[i];
+            it.rho = R->dfields;
+            it.e_g = R->dfields + N;
+            it.E_r = R->dfields + 2 * N;
+            it.T_g_out = R->dfields + 3 * N;
+            it.opacity = R->op;
+            it.eos = R->eos;
+            it.dt = R->dt;
+            it.bc = R->bc;
+            it.opts = R->opts;
+        }
+        bst = gq_batch_step(S->batch, S->items.data(), S->stream, binfo.data());
+        for (int i = 0; i < m; i++) S->infos[small[i]] = binfo[i];
+    }
     if (bst == GQ_ERR_CUDA || bst == GQ_ERR_INVALID_ARG) {
         // nothing ran: fail every resident request rather than retry forever
         for (ServeReq* R : S->active) {
@@ -287,6 +304,12 @@ gq_status gq_server_poll(gq_server* S, int* completed) {
         if (cur != S->device) cudaSetDevice(cur);
         if (completed) *completed = done;
         return bst;
+    }
+    for (int p : large) {
+        ServeReq* R = S->active[p];
+        const size_t N = (size_t)R->nx * R->ny;
+        gq_fld_step(R->plan, R->dfields, R->dfields + N, R->dfields + 2 * N, R->dfields + 3 * N, &R->op, &R->eos,
+                    R->dt, &R->bc, &R->opts, S->stream, &S->infos[p]);
     }
     // 3. retire finished or failed requests
     std::vector<ServeReq*> keep;

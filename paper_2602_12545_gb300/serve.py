@@ -45,10 +45,11 @@ class Completed:
 
 
 class FLDServer:
-    def __init__(self, budget_bytes: int, max_active: int = 256, use_graph: bool = False):
+    def __init__(self, budget_bytes: int, max_active: int = 256, use_graph: bool = False, solo_cells: int = 0):
         L = N.load()
         o = N.ServerOpts()
         o.budget_bytes, o.max_active, o.use_graph = int(budget_bytes), int(max_active), int(bool(use_graph))
+        o.solo_cells = int(solo_cells)
         h = ctypes.c_void_p()
         rc = L.gq_server_create(ctypes.byref(o), ctypes.byref(h))
         if rc != N.GQ_OK:
@@ -141,12 +142,13 @@ def _percentile(xs: List[float], q: float) -> float:
 
 
 def run_trace(trace: List[ServeRequest], budget_bytes: int, max_active: int = 256, keep_output=False,
-              opts: Optional[SolverOptions] = None, lookahead: int = 64, problem_fn=serve_problem) -> dict:
+              opts: Optional[SolverOptions] = None, lookahead: int = 64, problem_fn=serve_problem,
+              solo_cells: int = 0) -> dict:
     """Replay a trace in real time: request i is submitted when the wall clock reaches its
     arrival time (or as soon as its inputs are ready), the server is polled continuously,
     and latency is arrival -> completion.  Inputs are generated by a producer thread ahead
     of the clock (bounded lookahead)."""
-    srv = FLDServer(budget_bytes, max_active)
+    srv = FLDServer(budget_bytes, max_active, solo_cells=solo_cells)
     ready: deque = deque()
     lock = threading.Condition()
     stop = [False]

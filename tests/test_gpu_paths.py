@@ -107,12 +107,17 @@ def test_eos_table_subcycled(fld, orc, prec):
 # serving against sequential oracle steps
 # ----------------------------------------------------------------------------
 
-def test_served_requests_match_sequential_oracle_steps(fld, orc):
+@pytest.mark.parametrize("solo_cells", [-1, 3000])
+def test_served_requests_match_sequential_oracle_steps(fld, orc, solo_cells):
+    """solo_cells -1: every request in the batched launch; 3000: the requests of at least
+    3000 cells each step alone on the whole GPU after the batched launch of the others."""
     from paper_2602_12545_gb300 import serve as S
     rng = np.random.default_rng(41)
     reqs = [W.ServeRequest(i, 0.0, int(rng.integers(16, 120)), int(rng.integers(1, 5)), 4100 + i) for i in range(8)]
     probs = [W.serve_problem(r) for r in reqs]
-    srv = S.FLDServer(budget_bytes=8 << 30)
+    if solo_cells > 0:
+        assert any(P.ncells >= solo_cells for P in probs) and any(P.ncells < solo_cells for P in probs)
+    srv = S.FLDServer(budget_bytes=8 << 30, solo_cells=solo_cells)
     opts = fld.SolverOptions(prec=W.PREC_MIXED, limiter=W.LIMITER_LP, rtol=1e-10)
     ids = [srv.submit(P, r.n_steps, opts) for P, r in zip(probs, reqs)]
     res = {}
@@ -139,7 +144,7 @@ def test_served_requests_match_sequential_oracle_steps(fld, orc):
             Q = dataclasses.replace(Q, E_r=o["E_r"], e_g=o["e_g"])
         out = {"E_r": E, "T_g": T, "e_g": eg, "info": info}
         check_parity_conditioned(out, o, r.n_steps * MIXED_GATE, cond,
-                                 label=f"served {P.name} steps={r.n_steps}")
+                                 label=f"served {P.name} steps={r.n_steps} solo_cells={solo_cells}")
 
 
 # ----------------------------------------------------------------------------
