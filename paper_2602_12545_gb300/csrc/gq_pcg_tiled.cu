@@ -38,7 +38,7 @@ namespace gq {
 namespace {
 
 constexpr int kTiledThreads = 512;     // threads of a block (1024 measured slower: 64 registers, spills, costlier barriers)
-constexpr int kTX = 64, kTY = 16;      // tile of a level (cells)
+constexpr int kTX = 64, kTY = 32;      // tile of a level (cells); levels below kTallCells use kTY / 2
 constexpr int kHX = 4, kHY = 2;        // staged halo: x one 16-byte chunk, y two rows
 constexpr int kRW = kTX + 2 * kHX;     // staged region width (72)
 constexpr int kRH = kTY + 2 * kHY;     // staged region height (20)
@@ -49,7 +49,23 @@ constexpr int kNC = kCW * kCH;
 constexpr int kNT = kTX * kTY;         // cells of a tile
 constexpr int kStaged = 5;             // staged arrays with a halo
 constexpr int kOwn = 2;                // staged arrays of the tile alone
-constexpr int kNst = 3;                // pipeline depth: tiles staged ahead of the one computed
+constexpr int kNst = 2;                // pipeline depth: tiles staged ahead of the one computed
+constexpr int kTallCells = 1 << 18;    // levels of at least this many cells use kTY-high tiles
+
+// height of a level's tiles (host and device agree on it): tall tiles halve the halo and
+// the per-tile overhead on the large levels, short ones give the small levels more blocks
+__host__ __device__ __forceinline__ int tile_h(int cells) { return cells >= kTallCells ? kTY : kTY / 2; }
+
+// tile geometry of tile height TY (the shared-memory buffers are sized for kTY)
+template <int TY>
+struct Geo {
+    static constexpr int RH = TY + 2 * kHY;
+    static constexpr int NR = kRW * RH;
+    static constexpr int NT = kTX * TY;
+    static constexpr int CH = TY / 2 + 4;
+    static constexpr int NC = kCW * CH;
+    static constexpr unsigned HaloBytes = NR * 4, CoarseBytes = NC * 4, OwnBytes = NT * 4;
+};
 
 constexpr int kBlkCap = 1536;          // cells of the block levels kept in shared memory
 
@@ -86,7 +102,6 @@ enum { kMapR0 = 0, kMapR1, kMapCW, kMapCS, kMapT, kMapXA, kMapXC, kMapQ };
 constexpr int kOwnBase = kMaxTiledLevels * kMapsPerLevel;
 enum { kOwnP0 = 0, kOwnP1, kOwnD, kOwnZ, kOwnZold, kOwnCount };
 constexpr int kNumMaps = kOwnBase + kOwnCount;
-constexpr unsigned kHaloBytes = kNR * 4, kCoarseBytes = kNC * 4, kOwnBytes = kNT * 4;
 
 struct TiledMaps {
     CUtensorMap m[kNumMaps];
@@ -147,13 +162,15 @@ struct TLevel {
     int cnx, cny;              // parent dimensions
 };
 
-__device__ __forceinline__ int ntiles(const TLevel& L) { return ((L.nx + kTX - 1) / kTX) * ((L.ny + kTY - 1) / kTY); }
+template <int TY>
+__device__ __forceinline__ int ntiles(const TLevel& L) { return ((L.nx + kTX - 1) / kTX) * ((L.ny + TY - 1) / TY); }
 
+template <int TY>
 __device__ __forceinline__ void tile_origin(const TLevel& L, int t, int& x0, int& y0) {
     const int tx = (L.nx + kTX - 1) / kTX;
     const int ty = t / tx;
     x0 = (t - ty * tx) * kTX;
-    y0 = ty * kTY;
+    y0 = ty * TY;
 }
 
 // The tiles b, b + G, b + 2G, ... of a pass, each staged kNst - 1 tiles ahead of its
@@ -210,15 +227,17 @@ struct UpdateArgs {
 // Down pass of one level over all of its tiles this block owns (tiles b, b + G, ...).
 // Staged with a halo: 0 r (or r_old), 1 q (update only), 2 cW, 3 cS, 4 t; the tile
 // alone: 0 p, 1 d (update only).
+template <int TY>
 __device__ bool down_pass(const TLevel& L, float om, const UpdateArgs& U, TileSmem& S, const TiledMaps& M, TilePipe& pp,
                           int b, int G, double* rr) {
     // this thread's r'.r' over its cells of the pass, in FP32 (a few dozen terms; FP64
     // arithmetic per cell would cost more than the pass's memory traffic on this part)
     float rrf = 0.f;
-    const unsigned bytes = 4 * kHaloBytes + (U.on ? kHaloBytes + 2 * kOwnBytes : 0u);
+    using Gm = Geo<TY>;
+    const unsigned bytes = 4 * Gm::HaloBytes + (U.on ? Gm::HaloBytes + 2 * Gm::OwnBytes : 0u);
     auto issue = [&](int t, int buf) {
         int x0, y0;
-        tile_origin(L, t, x0, y0);
+        tile_origin<TY>(L, t, x0, y0);
         const int X0 = x0 - kHX, Y0 = y0 - kHY;
         unsigned long long* bar = &pp.bar[buf];
         fence_proxy_async();
@@ -235,7 +254,7 @@ __device__ bool down_pass(const TLevel& L, float om, const UpdateArgs& U, TileSm
     };
     auto compute = [&](int t, int buf) {
         int x0, y0;
-        tile_origin(L, t, x0, y0);
+        tile_origin<TY>(L, t, x0, y0);
         float* R = S.in[buf][0];
         const float* Q = S.in[buf][1];
         const float* CW = S.in[buf][2];
@@ -244,11 +263,11 @@ __device__ bool down_pass(const TLevel& L, float om, const UpdateArgs& U, TileSm
         float* XA = S.c1;
         if (U.on) {
             // r' = r - alpha q on the whole staged region (zeros stay zeros)
-            for (int e = threadIdx.x; e < kNR; e += blockDim.x) R[e] = R[e] - U.alpha * Q[e];
+            for (int e = threadIdx.x; e < Gm::NR; e += blockDim.x) R[e] = R[e] - U.alpha * Q[e];
             __syncthreads();
         }
         // x_a on the tile and a one-cell ring
-        constexpr int AW = kTX + 2, AH = kTY + 2;
+        constexpr int AW = kTX + 2, AH = TY + 2;
         for (int e = threadIdx.x; e < AW * AH; e += blockDim.x) {
             const int ly = e / AW, lx = e - ly * AW;
             const int ix = (kHY - 1 + ly) * kRW + (kHX - 1 + lx);
@@ -256,7 +275,7 @@ __device__ bool down_pass(const TLevel& L, float om, const UpdateArgs& U, TileSm
         }
         __syncthreads();
         // residual on the tile, restricted to the parent (one thread per 2 x 2 aggregate)
-        constexpr int CX = kTX / 2, CY = kTY / 2;
+        constexpr int CX = kTX / 2, CY = TY / 2;
         for (int e = threadIdx.x; e < CX * CY; e += blockDim.x) {
             const int cj = e / CX, ci = e - cj * CX;
             float acc = 0.f;
@@ -271,7 +290,7 @@ __device__ bool down_pass(const TLevel& L, float om, const UpdateArgs& U, TileSm
             if (gi < L.cnx && gj < L.cny) L.rc[(size_t)gj * L.cnx + gi] = acc;
         }
         // the tile's x_a (and, fused with the update, r', d and r'.r'), one cell a thread
-        for (int e = threadIdx.x; e < kNT; e += blockDim.x) {
+        for (int e = threadIdx.x; e < Gm::NT; e += blockDim.x) {
             const int ly = e / kTX, lx = e - ly * kTX;
             const int gx = x0 + lx, gy = y0 + ly;
             if (gx >= L.nx || gy >= L.ny) continue;
@@ -286,7 +305,7 @@ __device__ bool down_pass(const TLevel& L, float om, const UpdateArgs& U, TileSm
             }
         }
     };
-    const bool ok = tile_loop(ntiles(L), b, G, pp, issue, compute);
+    const bool ok = tile_loop(ntiles<TY>(L), b, G, pp, issue, compute);
     *rr += static_cast<double>(rrf);
     return ok;
 }
@@ -294,14 +313,16 @@ __device__ bool down_pass(const TLevel& L, float om, const UpdateArgs& U, TileSm
 // Up pass of one level.  Staged with a halo: 0 x_a, 1 t, 2 cW, 3 cS, 4 r; coarse: the
 // parent's result; the tile alone: 0 z_old (level 0).  Level 0 (zold != null): out is z,
 // with the partial sums r.z and r.z_old.
+template <int TY>
 __device__ bool up_pass(const TLevel& L, float om, float over, TileSmem& S, const TiledMaps& M, TilePipe& pp, int b,
                         int G, int mzold, double* rz, double* rzo) {
     float rzf = 0.f, rzof = 0.f;       // this thread's partial sums (FP32, see down_pass)
     const bool lvl0 = mzold >= 0;
-    const unsigned bytes = 5 * kHaloBytes + kCoarseBytes + (lvl0 ? kOwnBytes : 0u);
+    using Gm = Geo<TY>;
+    const unsigned bytes = 5 * Gm::HaloBytes + Gm::CoarseBytes + (lvl0 ? Gm::OwnBytes : 0u);
     auto issue = [&](int t, int buf) {
         int x0, y0;
-        tile_origin(L, t, x0, y0);
+        tile_origin<TY>(L, t, x0, y0);
         const int X0 = x0 - kHX, Y0 = y0 - kHY;
         unsigned long long* bar = &pp.bar[buf];
         fence_proxy_async();
@@ -316,7 +337,7 @@ __device__ bool up_pass(const TLevel& L, float om, float over, TileSmem& S, cons
     };
     auto compute = [&](int t, int buf) {
         int x0, y0;
-        tile_origin(L, t, x0, y0);
+        tile_origin<TY>(L, t, x0, y0);
         const float* XA = S.in[buf][0];
         const float* T = S.in[buf][1];
         const float* CW = S.in[buf][2];
@@ -329,7 +350,7 @@ __device__ bool up_pass(const TLevel& L, float om, float over, TileSmem& S, cons
         // parent of region cell (lx, ly) is coarse region cell ((lx - kHX) / 2 + 4,
         // (ly - kHY) / 2 + 2), with floor division (lx - kHX >= -2, ly - kHY >= -2)
         constexpr int AW = kTX + 4;
-        for (int e = threadIdx.x; e < AW * kRH; e += blockDim.x) {
+        for (int e = threadIdx.x; e < AW * Gm::RH; e += blockDim.x) {
             const int ly = e / AW, lx = kHX - 2 + (e - ly * AW);
             const int ix = ly * kRW + lx;
             const int pcx = ((lx - kHX + 2) >> 1) + 3, pcy = ((ly - kHY + 2) >> 1) + 1;
@@ -337,7 +358,7 @@ __device__ bool up_pass(const TLevel& L, float om, float over, TileSmem& S, cons
         }
         __syncthreads();
         // x_b on the tile and one ring
-        constexpr int BW = kTX + 2, BH = kTY + 2;
+        constexpr int BW = kTX + 2, BH = TY + 2;
         for (int e = threadIdx.x; e < BW * BH; e += blockDim.x) {
             const int ly = e / BW, lx = e - ly * BW;
             const int ix = (kHY - 1 + ly) * kRW + (kHX - 1 + lx);
@@ -345,7 +366,7 @@ __device__ bool up_pass(const TLevel& L, float om, float over, TileSmem& S, cons
         }
         __syncthreads();
         // the level's result on the tile, one cell a thread
-        for (int e = threadIdx.x; e < kNT; e += blockDim.x) {
+        for (int e = threadIdx.x; e < Gm::NT; e += blockDim.x) {
             const int ly = e / kTX, lx = e - ly * kTX;
             const int gx = x0 + lx, gy = y0 + ly;
             if (gx >= L.nx || gy >= L.ny) continue;
@@ -358,12 +379,24 @@ __device__ bool up_pass(const TLevel& L, float om, float over, TileSmem& S, cons
             }
         }
     };
-    const bool ok = tile_loop(ntiles(L), b, G, pp, issue, compute);
+    const bool ok = tile_loop(ntiles<TY>(L), b, G, pp, issue, compute);
     if (lvl0) {
         *rz += static_cast<double>(rzf);
         *rzo += static_cast<double>(rzof);
     }
     return ok;
+}
+
+// the tile height a level uses (see tile_h)
+__device__ __forceinline__ bool down_any(const TLevel& L, float om, const UpdateArgs& U, TileSmem& S,
+                                         const TiledMaps& M, TilePipe& pp, int b, int G, double* rr) {
+    return tile_h(L.nx * L.ny) == kTY ? down_pass<kTY>(L, om, U, S, M, pp, b, G, rr)
+                                      : down_pass<kTY / 2>(L, om, U, S, M, pp, b, G, rr);
+}
+__device__ __forceinline__ bool up_any(const TLevel& L, float om, float over, TileSmem& S, const TiledMaps& M,
+                                       TilePipe& pp, int b, int G, int mzold, double* rz, double* rzo) {
+    return tile_h(L.nx * L.ny) == kTY ? up_pass<kTY>(L, om, over, S, M, pp, b, G, mzold, rz, rzo)
+                                      : up_pass<kTY / 2>(L, om, over, S, M, pp, b, G, mzold, rz, rzo);
 }
 
 }  // namespace
@@ -477,7 +510,7 @@ __device__ bool tiled_solve(const SolveParams& P, const Workspace& w, RedShared&
         for (int l = pre0_done ? 1 : 0; l < lg; l++) {
             cyc_mark(msh.amg, team, l);
             double unused = 0.0;
-            if (!down_pass(tlevel(l), om, no_update, S, TM, pp, team.rank, team.size, &unused)) return false;
+            if (!down_any(tlevel(l), om, no_update, S, TM, pp, team.rank, team.size, &unused)) return false;
             if (!bar()) return false;
         }
         if (team.rank == 0 && blk_smem) {
@@ -554,11 +587,11 @@ __device__ bool tiled_solve(const SolveParams& P, const Workspace& w, RedShared&
         if (!bar()) return false;
         for (int l = lg - 1; l >= 1; l--) {
             cyc_mark(msh.amg, team, l);
-            if (!up_pass(tlevel(l), om, over, S, TM, pp, team.rank, team.size, -1, nullptr, nullptr)) return false;
+            if (!up_any(tlevel(l), om, over, S, TM, pp, team.rank, team.size, -1, nullptr, nullptr)) return false;
             if (!bar()) return false;
         }
         cyc_mark(msh.amg, team, 0);
-        if (!up_pass(tlevel(0), om, over, S, TM, pp, team.rank, team.size, kOwnBase + (zsel ? kOwnZ : kOwnZold), rz,
+        if (!up_any(tlevel(0), om, over, S, TM, pp, team.rank, team.size, kOwnBase + (zsel ? kOwnZ : kOwnZold), rz,
                      rzo))
             return false;
         cyc_mark(msh.amg, team, kAmgMaxLevels - 1);
@@ -871,7 +904,7 @@ __device__ bool tiled_solve(const SolveParams& P, const Workspace& w, RedShared&
                     // pnew is pb[cur] now (cur was flipped above)
                     const UpdateArgs upd{true, static_cast<float>(alpha), kMapQ, kOwnBase + kOwnP0 + cur,
                                          kOwnBase + kOwnD, q, pnew, d, rbuf[rsel ^ 1]};
-                    const bool okp = down_pass(tlevel(0), om, upd, S, TM, pp, team.rank, team.size, &v2[0]);
+                    const bool okp = down_any(tlevel(0), om, upd, S, TM, pp, team.rank, team.size, &v2[0]);
                     rsel ^= 1;
                     if (!okp) {
                         timed_out = true;
@@ -1029,6 +1062,7 @@ bool build_tiled_maps(const SolveParams& p, const Workspace& w, TiledMaps* M) {
         const MGLevel& L = mg.L[l];
         const MGLevel& C = mg.L[l + 1];
         CUtensorMap* m = M->m + l * kMapsPerLevel;
+        const int ty = tile_h(L.N), kRH = ty + 2 * kHY, kCH = ty / 2 + 4;
         const float* r0 = l == 0 ? w.r32 : L.r;
         ok = ok && encode(&m[kMapR0], r0, L.nx, L.ny, kRW, kRH);
         if (l == 0) ok = ok && encode(&m[kMapR1], w.r32b, L.nx, L.ny, kRW, kRH);
@@ -1041,6 +1075,7 @@ bool build_tiled_maps(const SolveParams& p, const Workspace& w, TiledMaps* M) {
     }
     const MGLevel& L0 = mg.L[0];
     CUtensorMap* o = M->m + kOwnBase;
+    const int kTY = tile_h(L0.N);
     ok = ok && encode(&o[kOwnP0], w.p32[0], L0.nx, L0.ny, kTX, kTY);
     ok = ok && encode(&o[kOwnP1], w.p32[1], L0.nx, L0.ny, kTX, kTY);
     ok = ok && encode(&o[kOwnD], w.d32, L0.nx, L0.ny, kTX, kTY);
