@@ -158,13 +158,16 @@ def spherical_fields(xf: np.ndarray, yf: np.ndarray, rng: np.random.Generator):
 
 def config2(seed: int = 1002, nr: int = 2048, nth: int = 1024) -> FLDProblem:
     """2048 (r, log-spaced 1e11..1e14 cm) x 1024 (theta, 0..pi) spherical-polar, dt = 1e4 s,
-    reflecting at inner r and theta ends, Milne at outer r, mixed precision to 1e-8."""
+    reflecting at inner r and theta ends, Milne at outer r, mixed precision with a
+    cell-wise residual of 2e-10: the loosest setting (of 1e-11, 3e-11, 1e-10, 2e-10, 3e-10,
+    1e-9 measured) that keeps every cell within 1e-8 of the tightly solved answer with
+    room to spare (2.2e-9 measured; 1e-9 gives 3.7e-8)."""
     rng = np.random.default_rng(seed)
     xf = log_faces(nr, 1e11, 1e14)
     yf = theta_faces(nth)
     rho, T, Trad = spherical_fields(xf, yf, rng)
     return _pack("c2_sph2048x1024", SPHERICAL, xf, yf, rho, T, Trad, 1e4,
-                 bc=(BC_REFLECT, BC_MILNE, BC_REFLECT, BC_REFLECT), precision=PREC_MIXED, rtol=1e-8)
+                 bc=(BC_REFLECT, BC_MILNE, BC_REFLECT, BC_REFLECT), precision=PREC_MIXED, rtol=2e-10)
 
 
 def batch_sizes(n_problems: int = 256, seed: int = 1003):
