@@ -5,8 +5,9 @@
 //
 // A pass walks the level in tiles of kTX x kTY cells.  Each block stages a tile's inputs
 // with a halo (kHX = 4 cells in x, one 16-byte chunk; kHY = 2 rows in y) into shared
-// memory by cp.async (zero-filled outside the grid, double-buffered so that the next
-// tile's loads overlap this tile's arithmetic), and computes what needs neighbours from
+// memory by TMA tensor copies (cp.async.bulk.tensor, one per array, completing on an
+// mbarrier; boxes outside the grid read zeros; double-buffered so that the next tile's
+// loads overlap this tile's arithmetic), and computes what needs neighbours from
 // the staged copy, redundantly on the halo:
 //   down pass (level l):  x_a = omega (2 r - omega A r) on the tile and a one-cell ring,
 //                         then the residual r - A x_a on the tile, restricted to level
@@ -41,15 +42,15 @@ constexpr int kTiledThreads = 512;     // threads of a block (1024 measured slow
 constexpr int kTX = 64, kTY = 32;      // tile of a level (cells); levels below kTallCells use kTY / 2
 constexpr int kHX = 4, kHY = 2;        // staged halo: x one 16-byte chunk, y two rows
 constexpr int kRW = kTX + 2 * kHX;     // staged region width (72)
-constexpr int kRH = kTY + 2 * kHY;     // staged region height (20)
+constexpr int kRH = kTY + 2 * kHY;     // staged region height (36)
 constexpr int kNR = kRW * kRH;
-constexpr int kCW = kTX / 2 + 8;       // staged coarse region (40 x 12)
+constexpr int kCW = kTX / 2 + 8;       // staged coarse region (40 x 20)
 constexpr int kCH = kTY / 2 + 4;
 constexpr int kNC = kCW * kCH;
 constexpr int kNT = kTX * kTY;         // cells of a tile
 constexpr int kStaged = 5;             // staged arrays with a halo
 constexpr int kOwn = 2;                // staged arrays of the tile alone
-constexpr int kNst = 2;                // pipeline depth: tiles staged ahead of the one computed
+constexpr int kNst = 2;                // staging buffers: the tile computed and kNst - 1 tiles ahead
 constexpr int kTallCells = 1 << 18;    // levels of at least this many cells use kTY-high tiles
 
 // height of a level's tiles (host and device agree on it): tall tiles halve the halo and
