@@ -132,10 +132,13 @@ __device__ __forceinline__ void tma2d(void* dst, const CUtensorMap* map, int x, 
         "l"(map), "r"(x), "r"(y), "r"(smem_u32(b))
         : "memory");
 }
-// orders this thread's view of memory (generic stores of other blocks acquired at the last grid
-// barrier, generic reads of a buffer before the copies that overwrite it) before its next
-// tensor copies
+// Proxy fences of the issuing thread.  The full one orders the generic stores of earlier passes
+// (other blocks' stores acquired at the grid barrier before this pass, this block's generic
+// use of the staging buffers) before this pass's tensor copies: once per pass, because no
+// pass reads by tensor copy what the same pass stores.  The shared-memory one orders the
+// block's generic reads of a staging buffer before the copies that refill it: once per tile.
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
 // The mbarriers of the staging buffers and the phase each is in (identical in every thread).
 struct TilePipe {
@@ -181,6 +184,7 @@ __device__ __forceinline__ void tile_origin(const TLevel& L, int t, int& x0, int
 template <class Issue, class Compute>
 __device__ __forceinline__ bool tile_loop(int nt, int b, int G, TilePipe& pp, Issue issue, Compute compute) {
     if (threadIdx.x == 0) {
+        fence_proxy_async();
 #pragma unroll
         for (int k = 0; k < kNst - 1; k++) {
             const int t = b + k * G;
@@ -241,7 +245,7 @@ __device__ bool down_pass(const TLevel& L, float om, const UpdateArgs& U, TileSm
         tile_origin<TY>(L, t, x0, y0);
         const int X0 = x0 - kHX, Y0 = y0 - kHY;
         unsigned long long* bar = &pp.bar[buf];
-        fence_proxy_async();
+        fence_proxy_async_smem();
         mbar_expect(bar, bytes);
         tma2d(S.in[buf][0], &M.m[L.mr], X0, Y0, bar);
         tma2d(S.in[buf][2], &M.m[L.mcw], X0, Y0, bar);
@@ -326,7 +330,7 @@ __device__ bool up_pass(const TLevel& L, float om, float over, TileSmem& S, cons
         tile_origin<TY>(L, t, x0, y0);
         const int X0 = x0 - kHX, Y0 = y0 - kHY;
         unsigned long long* bar = &pp.bar[buf];
-        fence_proxy_async();
+        fence_proxy_async_smem();
         mbar_expect(bar, bytes);
         tma2d(S.in[buf][0], &M.m[L.mxa], X0, Y0, bar);
         tma2d(S.in[buf][1], &M.m[L.mt], X0, Y0, bar);
