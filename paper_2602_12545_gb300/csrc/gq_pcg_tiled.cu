@@ -48,6 +48,8 @@ constexpr int kCW = kTX / 2 + 8;       // staged coarse region (40 x 20)
 constexpr int kCH = kTY / 2 + 4;
 constexpr int kNC = kCW * kCH;
 constexpr int kNT = kTX * kTY;         // cells of a tile
+constexpr int kRG = kRW / 4;           // groups of 4 cells in a staged region row (18)
+constexpr int kTG = kTX / 4;           // groups of 4 cells in a tile row (16)
 constexpr int kStaged = 5;             // staged arrays with a halo
 constexpr int kOwn = 2;                // staged arrays of the tile alone
 constexpr int kNst = 2;                // staging buffers: the tile computed and kNst - 1 tiles ahead
@@ -147,9 +149,36 @@ struct TilePipe {
     long long spin;            // poll limit of a wait
 };
 
-// (A v) at region index i: unit diagonal, couplings staged like v
-__device__ __forceinline__ float st5(const float* v, const float* cw, const float* cs, int i) {
-    return v[i] - cw[i] * v[i - 1] - cw[i + 1] * v[i + 1] - cs[i] * v[i - kRW] - cs[i + kRW] * v[i + kRW];
+// The tile passes work on groups of 4 cells of a region row (region index a multiple of
+// 4, so every staged and computed array is read and written as float4): a group's
+// stencil takes 6 vector and 3 scalar shared-memory loads instead of 36 scalar ones.
+__device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void sts4(float* p, const float4& v) { *reinterpret_cast<float4*>(p) = v; }
+
+// (A v) on the 4 cells at region index i (i % 4 == 0, a row with rows above and below in
+// the region): unit diagonal and couplings staged like v, per cell k
+//   v_k - cW_k v_{k-1} - cW_{k+1} v_{k+1} - cS_k v_{k-kRW} - cS_{k+kRW} v_{k+kRW}
+__device__ __forceinline__ float4 st5x4(const float* v, const float* cw, const float* cs, int i) {
+    const float4 c = lds4(v + i), s = lds4(v + i - kRW), n = lds4(v + i + kRW);
+    const float w = v[i - 1], e = v[i + 4];
+    const float4 a = lds4(cw + i), b = lds4(cs + i), bn = lds4(cs + i + kRW);
+    const float ae = cw[i + 4];
+    float4 r;
+    r.x = c.x - a.x * w - a.y * c.y - b.x * s.x - bn.x * n.x;
+    r.y = c.y - a.y * c.x - a.z * c.z - b.y * s.y - bn.y * n.y;
+    r.z = c.z - a.z * c.y - a.w * c.w - b.z * s.z - bn.z * n.z;
+    r.w = c.w - a.w * c.z - ae * e - b.w * s.w - bn.w * n.w;
+    return r;
+}
+
+__device__ __forceinline__ float4 axpy4(const float4& x, float a, const float4& y) {   // x + a y
+    return make_float4(x.x + a * y.x, x.y + a * y.y, x.z + a * y.z, x.w + a * y.w);
+}
+__device__ __forceinline__ float4 sub4(const float4& x, const float4& y) {
+    return make_float4(x.x - y.x, x.y - y.y, x.z - y.z, x.w - y.w);
+}
+__device__ __forceinline__ float dot4(const float4& x, const float4& y) {
+    return x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w;
 }
 
 struct TLevel {
@@ -268,45 +297,47 @@ __device__ bool down_pass(const TLevel& L, float om, const UpdateArgs& U, TileSm
         float* XA = S.c1;
         if (U.on) {
             // r' = r - alpha q on the whole staged region (zeros stay zeros)
-            for (int e = threadIdx.x; e < Gm::NR; e += blockDim.x) R[e] = R[e] - U.alpha * Q[e];
+#pragma unroll
+            for (int e = threadIdx.x; e < Gm::NR / 4; e += kTiledThreads)
+                sts4(R + 4 * e, axpy4(lds4(R + 4 * e), -U.alpha, lds4(Q + 4 * e)));
             __syncthreads();
         }
-        // x_a on the tile and a one-cell ring
-        constexpr int AW = kTX + 2, AH = TY + 2;
-        for (int e = threadIdx.x; e < AW * AH; e += blockDim.x) {
-            const int ly = e / AW, lx = e - ly * AW;
-            const int ix = (kHY - 1 + ly) * kRW + (kHX - 1 + lx);
-            XA[ix] = om * (2.f * R[ix] - om * st5(R, CW, CS, ix));
+        // x_a on the tile and a one-cell ring (whole region rows: the groups at the row ends
+        // are formed too and never read)
+#pragma unroll
+        for (int e = threadIdx.x; e < (TY + 2) * kRG; e += kTiledThreads) {
+            const int ly = e / kRG, g = e - ly * kRG;
+            const int ix = (kHY - 1 + ly) * kRW + 4 * g;
+            const float4 r = lds4(R + ix), a = st5x4(R, CW, CS, ix);
+            sts4(XA + ix, make_float4(om * (2.f * r.x - om * a.x), om * (2.f * r.y - om * a.y),
+                                      om * (2.f * r.z - om * a.z), om * (2.f * r.w - om * a.w)));
         }
         __syncthreads();
-        // residual on the tile, restricted to the parent (one thread per 2 x 2 aggregate)
-        constexpr int CX = kTX / 2, CY = TY / 2;
-        for (int e = threadIdx.x; e < CX * CY; e += blockDim.x) {
-            const int cj = e / CX, ci = e - cj * CX;
-            float acc = 0.f;
-#pragma unroll
-            for (int dy = 0; dy < 2; dy++)
-#pragma unroll
-                for (int dx = 0; dx < 2; dx++) {
-                    const int ix = (kHY + 2 * cj + dy) * kRW + (kHX + 2 * ci + dx);
-                    acc += T[ix] * (R[ix] - st5(XA, CW, CS, ix));
+        // the tile, a group a thread: the residual restricted to the parent (the two rows of
+        // an aggregate are lanes l and l + 16 of one warp), x_a and, fused with the update,
+        // r', d and r'.r'
+        if (threadIdx.x < TY * kTG) {
+            const int ly = threadIdx.x / kTG, g = threadIdx.x - ly * kTG;
+            const int ix = (kHY + ly) * kRW + kHX + 4 * g;
+            const float4 r = lds4(R + ix), tw = lds4(T + ix), res = sub4(r, st5x4(XA, CW, CS, ix));
+            float c0 = tw.x * res.x + tw.y * res.y, c1 = tw.z * res.z + tw.w * res.w;
+            c0 += __shfl_down_sync(0xffffffffu, c0, kTG);
+            c1 += __shfl_down_sync(0xffffffffu, c1, kTG);
+            const int gx = x0 + 4 * g, gy = y0 + ly;
+            if ((ly & 1) == 0) {
+                const int gi = gx / 2, gj = gy / 2;
+                if (gi < L.cnx && gj < L.cny)
+                    *reinterpret_cast<float2*>(L.rc + (size_t)gj * L.cnx + gi) = make_float2(c0, c1);
+            }
+            if (gx < L.nx && gy < L.ny) {
+                const size_t gg = (size_t)gy * L.nx + gx;
+                sts4(L.xa + gg, lds4(XA + ix));
+                if (U.on) {
+                    const int o = ly * kTX + 4 * g;
+                    sts4(U.rnew + gg, r);
+                    sts4(U.d + gg, axpy4(lds4(S.own[buf][1] + o), U.alpha, lds4(S.own[buf][0] + o)));
+                    rrf += dot4(r, r);
                 }
-            const int gi = x0 / 2 + ci, gj = y0 / 2 + cj;
-            if (gi < L.cnx && gj < L.cny) L.rc[(size_t)gj * L.cnx + gi] = acc;
-        }
-        // the tile's x_a (and, fused with the update, r', d and r'.r'), one cell a thread
-        for (int e = threadIdx.x; e < Gm::NT; e += blockDim.x) {
-            const int ly = e / kTX, lx = e - ly * kTX;
-            const int gx = x0 + lx, gy = y0 + ly;
-            if (gx >= L.nx || gy >= L.ny) continue;
-            const int ix = (kHY + ly) * kRW + (kHX + lx);
-            const size_t g = (size_t)gy * L.nx + gx;
-            L.xa[g] = XA[ix];
-            if (U.on) {
-                const float rn = R[ix];
-                U.rnew[g] = rn;
-                U.d[g] = S.own[buf][1][e] + U.alpha * S.own[buf][0][e];
-                rrf += rn * rn;
             }
         }
     };
@@ -351,36 +382,44 @@ __device__ bool up_pass(const TLevel& L, float om, float over, TileSmem& S, cons
         const float* C = S.co[buf];
         float* XT = S.c1;
         float* XB = S.c2;
-        // x~ on the tile and two rings: region columns kHX-2 .. kHX+kTX+1, all rows; the
-        // parent of region cell (lx, ly) is coarse region cell ((lx - kHX) / 2 + 4,
-        // (ly - kHY) / 2 + 2), with floor division (lx - kHX >= -2, ly - kHY >= -2)
-        constexpr int AW = kTX + 4;
-        for (int e = threadIdx.x; e < AW * Gm::RH; e += blockDim.x) {
-            const int ly = e / AW, lx = kHX - 2 + (e - ly * AW);
-            const int ix = ly * kRW + lx;
-            const int pcx = ((lx - kHX + 2) >> 1) + 3, pcy = ((ly - kHY + 2) >> 1) + 1;
-            XT[ix] = XA[ix] + over * T[ix] * C[pcy * kCW + pcx];
+        // x~ on the whole region (the tile and two rings are read); the parent of region
+        // cell (lx, ly) is coarse region cell ((lx - kHX) / 2 + 4, (ly - kHY) / 2 + 2), floor
+        // division: cells 4g, 4g + 1 of a row have parent column 2g + 2, cells 4g + 2, 4g + 3
+        // parent column 2g + 3
+#pragma unroll
+        for (int e = threadIdx.x; e < Gm::RH * kRG; e += kTiledThreads) {
+            const int ly = e / kRG, g = e - ly * kRG;
+            const int ix = ly * kRW + 4 * g;
+            const float2 c = *reinterpret_cast<const float2*>(C + (((ly - kHY) >> 1) + 2) * kCW + 2 * g + 2);
+            const float4 xa = lds4(XA + ix), tw = lds4(T + ix);
+            sts4(XT + ix, make_float4(xa.x + over * tw.x * c.x, xa.y + over * tw.y * c.x, xa.z + over * tw.z * c.y,
+                                      xa.w + over * tw.w * c.y));
         }
         __syncthreads();
-        // x_b on the tile and one ring
-        constexpr int BW = kTX + 2, BH = TY + 2;
-        for (int e = threadIdx.x; e < BW * BH; e += blockDim.x) {
-            const int ly = e / BW, lx = e - ly * BW;
-            const int ix = (kHY - 1 + ly) * kRW + (kHX - 1 + lx);
-            XB[ix] = XT[ix] + om * (R[ix] - st5(XT, CW, CS, ix));
+        // x_b on the tile and one ring (whole region rows)
+#pragma unroll
+        for (int e = threadIdx.x; e < (TY + 2) * kRG; e += kTiledThreads) {
+            const int ly = e / kRG, g = e - ly * kRG;
+            const int ix = (kHY - 1 + ly) * kRW + 4 * g;
+            const float4 r = lds4(R + ix), x = lds4(XT + ix), a = st5x4(XT, CW, CS, ix);
+            sts4(XB + ix, make_float4(x.x + om * (r.x - a.x), x.y + om * (r.y - a.y), x.z + om * (r.z - a.z),
+                                      x.w + om * (r.w - a.w)));
         }
         __syncthreads();
-        // the level's result on the tile, one cell a thread
-        for (int e = threadIdx.x; e < Gm::NT; e += blockDim.x) {
-            const int ly = e / kTX, lx = e - ly * kTX;
-            const int gx = x0 + lx, gy = y0 + ly;
-            if (gx >= L.nx || gy >= L.ny) continue;
-            const int ix = (kHY + ly) * kRW + (kHX + lx);
-            const float o = XB[ix] + om * (R[ix] - st5(XB, CW, CS, ix));
-            L.out[(size_t)gy * L.nx + gx] = o;
-            if (lvl0) {
-                rzf += R[ix] * o;
-                rzof += R[ix] * S.own[buf][0][e];
+        // the level's result on the tile, a group a thread
+        if (threadIdx.x < TY * kTG) {
+            const int ly = threadIdx.x / kTG, g = threadIdx.x - ly * kTG;
+            const int ix = (kHY + ly) * kRW + kHX + 4 * g;
+            const float4 r = lds4(R + ix), x = lds4(XB + ix), a = st5x4(XB, CW, CS, ix);
+            const float4 o = make_float4(x.x + om * (r.x - a.x), x.y + om * (r.y - a.y), x.z + om * (r.z - a.z),
+                                         x.w + om * (r.w - a.w));
+            const int gx = x0 + 4 * g, gy = y0 + ly;
+            if (gx < L.nx && gy < L.ny) {
+                sts4(L.out + (size_t)gy * L.nx + gx, o);
+                if (lvl0) {
+                    rzf += dot4(r, o);
+                    rzof += dot4(r, lds4(S.own[buf][0] + ly * kTX + 4 * g));
+                }
             }
         }
     };
