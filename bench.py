@@ -90,6 +90,8 @@ def parse():
     ap.add_argument("--untiled", action="store_true", help="use the untiled solve kernel (comparison)")
     ap.add_argument("--block-cells", type=int, default=0,
                     help="multigrid levels of at most this many cells run in one block (0: library default)")
+    ap.add_argument("--inner-rtol", type=float, default=None,
+                    help="mixed precision: FP32 residual drop that triggers an FP64 refinement (default: library's)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
@@ -307,8 +309,9 @@ def run_ours(args):
         info["ms"] = s0.elapsed_time(s1)
         return info
 
+    extra = {} if args.inner_rtol is None else {"inner_rtol": args.inner_rtol}
     opts = F.SolverOptions(prec=prec, limiter=P.limiter, rtol=rtol, timing=1, precond=args.precond,
-                           untiled=int(args.untiled), mg_block_cells=args.block_cells)
+                           untiled=int(args.untiled), mg_block_cells=args.block_cells, **extra)
     # accuracy reference: FP64 path solved tightly (untimed)
     ref_opts = F.SolverOptions(prec=0, limiter=P.limiter, rtol=1e-13, timing=0, max_iter=1000000)
     ref_info = one(ref_opts, check=False)       # may stop at the FP64 floor (status 4)
