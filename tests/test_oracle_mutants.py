@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 import test_oracle_adv as ADV
+import test_oracle_conventions as CONV
 import test_oracle_eos as EOS
 import test_oracle_opacity as OPA
 
@@ -54,6 +55,28 @@ MUTANTS = {
     "beta_from_rosseland": ("W->betaP[k] = kP * rho * c * P->dt;",
                             "W->betaP[k] = kR * rho * c * P->dt;",
                             OPA.test_planck_law_in_the_exchange_closed_form),
+    # face interpolation weights the wrong way round (sigma, E taken at the mirrored point)
+    "face_interpolation_mirrored": ("double th = (P->xf[i] - xk) / d;",
+                                    "double th = (xm - P->xf[i]) / d;",
+                                    CONV.test_face_values_interpolate_linear_fields_exactly_cartesian),
+    # theta distance without the radius (d = dtheta_c instead of r_c dtheta_c)
+    "theta_distance_without_r": ("double d = metric * (ym - yk);",
+                                 "double d = (ym - yk);",
+                                 CONV.test_spherical_face_fluxes_converge_at_second_order),
+    # theta distance at the inner face radius instead of the volume centroid's
+    "theta_distance_inner_radius": ("double d = metric * (ym - yk);",
+                                    "double d = (P->coord == 1 ? P->xf[i] : 1.0) * (ym - yk);",
+                                    CONV.test_spherical_face_fluxes_converge_at_second_order),
+    # Milne ghost: the full cell width instead of the half-cell distance to the face
+    "milne_full_cell": ("double h = fabs(P->xf[i] - W->xc[ic]);",
+                        "double h = 2.0 * fabs(P->xf[i] - W->xc[ic]);",
+                        CONV.test_milne_eigenmode_decays_as_the_continuum_one),
+    # Milne ghost: 1/(3 sigma) in place of the 2/(3 sigma) of Eq. milne (x sides)
+    "milne_factor": ("double kk = 2.0 / (3.0 * s * h);\n                double D = c * orc_limiter(P->limiter, 1.5) / s;\n"
+                     "                W->Rx[f] = 1.5;",
+                     "double kk = 1.0 / (3.0 * s * h);\n                double D = c * orc_limiter(P->limiter, 1.5) / s;\n"
+                     "                W->Rx[f] = 1.5;",
+                     CONV.test_milne_eigenmode_decays_as_the_continuum_one),
 }
 
 
