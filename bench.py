@@ -84,6 +84,8 @@ def parse():
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: mean arrival rate (1/s)")
     ap.add_argument("--budget-gb", type=float, default=60.0, help="serving: device memory budget")
     ap.add_argument("--rtol", type=float, default=None)
+    ap.add_argument("--c2-grid", default=None,
+                    help="NRxNTH: draw the spherical workload on a smaller grid (profiling captures only)")
     ap.add_argument("--precond", type=int, default=None,
                     help="0 Jacobi, 1 aggregation multigrid, 2 algebraic multigrid (default: per workload)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison path")
@@ -102,8 +104,15 @@ def parse():
     return args
 
 
-def workload(name):
+def workload(name, c2_grid=None):
+    """The named workload; c2_grid = (nr, ntheta) draws the spherical one's fields on a
+    smaller grid (profiling captures; the benchmark's line uses 2048 x 1024)."""
     from paper_2602_12545_gb300 import workloads as W
+    if name == "c2" and c2_grid is not None:
+        nr, nth = c2_grid
+        P = W.config2(nr=nr, nth=nth)
+        return P, (f"{nr} (r, log 1e11-1e14 cm) x {nth} (theta 0-pi) spherical-polar, Milne at outer r, "
+                   "dt=1e4 s (reduced grid)")
     P = {"c0": W.config0, "c1": W.config1, "c2": W.config2}[name]()
     desc = {"c0": "64x64 uniform Cartesian, reflecting, dt=1e4 s",
             "c1": "1024x1024 Cartesian, dx geometric x1.002, Milne at +x, dt=1e5 s",
@@ -283,7 +292,8 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    P, desc = workload(args.workload)
+    c2_grid = tuple(int(v) for v in args.c2_grid.lower().split("x")) if args.c2_grid else None
+    P, desc = workload(args.workload, c2_grid)
     # the workload's cell-wise residual target (for the spherical grid the loosest setting
     # whose E and T agree with the tightly solved FP64 answer to 1e-8 per cell, reported)
     rtol = args.rtol if args.rtol is not None else P.rtol
