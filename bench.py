@@ -111,6 +111,7 @@ def workload(name, c2_grid=None):
     if name == "c2" and c2_grid is not None:
         nr, nth = c2_grid
         P = W.config2(nr=nr, nth=nth)
+        P.name = f"c2_sph{nr}x{nth}"
         return P, (f"{nr} (r, log 1e11-1e14 cm) x {nth} (theta 0-pi) spherical-polar, Milne at outer r, "
                    "dt=1e4 s (reduced grid)")
     P = {"c0": W.config0, "c1": W.config1, "c2": W.config2}[name]()
@@ -379,7 +380,8 @@ def run_ours(args):
     peak, peak_kind = peaks()
     tag = ("pcg_tiled_c2" if solve_kernel == "k_pcg_tiled" else
            f"pcg_{'mixed' if prec else 'fp64'}_{args.workload}")
-    traffic = traffic_from_profile(tag, kernel_source_hash())
+    # the committed DRAM figure is for the full-size grid: none for a reduced one
+    traffic = traffic_from_profile(tag, kernel_source_hash()) if c2_grid is None else None
     if traffic is not None:
         traffic = traffic
 
