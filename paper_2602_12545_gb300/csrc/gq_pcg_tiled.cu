@@ -765,10 +765,14 @@ __device__ bool tiled_solve(const SolveParams& P, const Workspace& w, RedShared&
             }
             // the FP64 residual b^ - A^ y, written straight to the FP32 Krylov residual
             // (times the fixed scale zs), with its FP32 square sum and the cell-wise
-            // criterion: the only FP64 arithmetic per cell is the stencil, the scaling
-            // and the criterion's quotient (this part's FP64 rate is a sixtieth of FP32)
+            // criterion: the only FP64 arithmetic per cell is the stencil and two
+            // scalings (this part's FP64 rate is a sixtieth of FP32).  The criterion's
+            // quotient |r_k / y_k| is taken in FP32 from the scaled r_k zs and y_k zs
+            // where both lie well inside the FP32 range (to about two FP32 ulps, as
+            // abs_ratio_approx), otherwise (tiny or huge y_k, zero, inf, NaN) from the
+            // FP64 values by abs_ratio_approx.
             {
-                float rrf = 0.f;
+                float rrf = 0.f, crf = 0.f;
                 double cr[2] = {0.0, 0.0};
                 float* r0 = rbuf[rsel];
                 for (int c = tid; c < N / 2; c += stride) {
@@ -799,11 +803,16 @@ __device__ bool tiled_solve(const SolveParams& P, const Workspace& w, RedShared&
                         const double rk = bk[i] - (yc[i] - cw[i] * left - cright * right - cs[i] * ys[i] - csn[i] * yn[i]);
                         f[i] = static_cast<float>(rk * zs);
                         rrf += f[i] * f[i];
-                        cr[1] = nanmax(cr[1], abs_ratio_approx(rk, yc[i]));
+                        const float fr = fabsf(f[i]), fy = fabsf(static_cast<float>(yc[i] * zs));
+                        const float qk = (fy >= 1e-8f && fy <= 1e30f && fr <= 1e30f)
+                                             ? __fdividef(fr, fy)
+                                             : static_cast<float>(abs_ratio_approx(rk, yc[i]));
+                        crf = (crf != crf || qk != qk) ? qk + crf : fmaxf(crf, qk);
                     }
                     stf<2>(r0 + k, f);
                 }
                 cr[0] = static_cast<double>(rrf);
+                cr[1] = static_cast<double>(crf);
                 if (!allreduce<1, 1>(cr, w.partials, parity, w.bar, P.spin_limit, abort_flag, sh, team)) {
                     timed_out = true;
                     return false;
